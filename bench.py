@@ -1,0 +1,368 @@
+"""Benchmark of the GB300 time-spectral GLS hot path (one JSON line on rank 0).
+
+Workload: the Fontan-like synthetic cross junction (two inlets of radius
+1.0 and 0.8, two outlets of radius 0.9, arm length 6), seeded tetrahedral
+mesh of about 188k tets / 38k nodes, N = 7 modes, Re 500, Wo 10, random 1/k^2
+inflow waveforms, resistance outlets R = 1.
+
+A step is one pseudo-time Newton-GMRES step of the mixed-precision solver
+through the C ABI (``ts_solve``): the FP64 residual of eq. (Rmc) with tau
+at every quadrature point, an approximate-diagonal right preconditioner, and
+GMRES with a fixed budget of KRYLOV FP32 tangent products (eq. K_mat, tau
+frozen, A linearised) and FP64 classical Gram-Schmidt, then the update.
+``value`` = element-mode operator evaluations per second, E * N * (tangent
+products + residuals) / time.  The time to ||r|| <= 1e-8 r_ref of the full
+solve, mixed vs FP64, is measured once beside the timed steps.
+
+``--impl reference`` times the CPU oracle (FP64 numpy, complex modes) on the
+host cores on a bounded element sample of the same workload, same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")   # the CPU oracle runs on one core
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+
+import numpy as np
+
+METRIC = "GLS operator element-mode evals/s; time to 1e-8 residual, mixed vs FP64 on GB300"
+KRYLOV = 30
+N_MODES = 7
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _workload(seed_mesh=1, h=0.123):
+    from workloads import cases, meshgen as mg
+    mesh = mg.junction(h=h, seed=seed_mesh)
+    return cases.junction_case(N=N_MODES, Re=500.0, Wo=10.0, wave_seed=100, resistance=1.0, mesh=mesh)
+
+
+def _config(case, extra=None):
+    c = {"workload": "fontan-like cross junction, P1-P1 tets, time-spectral GLS Navier-Stokes",
+         "n_tets": int(case.mesh.n_tets), "n_nodes": int(case.mesh.n_nodes), "n_modes": case.N,
+         "Re": 500.0, "Wo": 10.0, "outlets": "resistance R=1",
+         "step": f"1 pseudo-time Newton step: FP64 residual + {KRYLOV} FP32 tangent products in FP64 GMRES",
+         "l2": "inputs larger than L2 (tau cache 0.27 GB, Krylov basis 0.5 GB)"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index=0):
+        self.samples, self.proc, self.thread = [], None, None
+        self.index = index
+
+    def start(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+
+        def rd():
+            for line in self.proc.stdout:
+                self.samples.append([x.strip() for x in line.split(",")])
+        self.thread = threading.Thread(target=rd, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            try:
+                sm.append(float(s[0]))
+                mx.append(float(s[1]))
+                for k, n in enumerate(names):
+                    if s[3 + k].lower().startswith("active"):
+                        reasons.add(n)
+            except Exception:
+                pass
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(mx)) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _jvp_bytes(case, b=4):
+    """Algorithmic bytes of one tangent product (eq. K_mat, LIN_A variant)."""
+    V, E, N = case.mesh.n_nodes, case.mesh.n_tets, case.N
+    nm = 2 * N - 1
+    return (V * 8 * N * b          # v
+            + V * 8 * N * b        # linearisation state u0, p0 (LIN_A reads both)
+            + V * 8 * N * b        # Hv
+            + 16 * E               # connectivity
+            + 12 * V               # coordinates (geometry)
+            + E * 4 * nm * (nm + 1) // 2 * b   # tau per quadrature point
+            + E * 4 * 3 * 2 * N * b)           # tau L(u0) per point (LIN_A)
+
+
+def _profile_traffic(kernel_src):
+    """DRAM traffic per tangent product from the committed ncu summary, if still current."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "apply_jvp_traffic.json")) as f:
+            d = json.load(f)
+        h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+        if d.get("source_sha") == h:
+            return float(d["dram_bytes_per_jvp"])
+    except Exception:
+        pass
+    return None
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        dist.init_process_group(backend=backend)
+        return dist, rank, ws
+    return None, rank, ws
+
+
+def _max_over_ranks(dist, x):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_gpu(args):
+    import torch
+
+    import paper_2311_09465_gb300 as ts
+
+    dist, rank, ws = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    case = _workload()
+    E, N = case.mesh.n_tets, case.N
+    g = ts.GLSProblem(case, variant="lin_a", dt_pseudo=args.dt)
+    stream = torch.cuda.current_stream()
+    y = torch.tensor(case.y0, dtype=torch.float64, device="cuda")
+    opts = dict(precision=32, tol=1e-300, max_steps=1, krylov=KRYLOV, eps_ls=1e-30,
+                max_matvec=KRYLOV, precond=1, raise_on_noconv=False)
+    # warm-up: pseudo-time steps from the plain initial guess
+    for _ in range(args.warmup):
+        g.solve(y, **opts)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K pseudo-time steps in one solve call
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = ts.ts_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    rep = g.solve(y, **dict(opts, max_steps=args.steps))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    launches = ts.ts_launch_count() - l0
+    clk = clocks.stop()
+    t_total = ev0.elapsed_time(ev1) / 1e3
+    t_total = _max_over_ranks(dist, t_total)
+    ops = rep["matvecs"] + rep["steps"] + 1          # tangent products + residuals
+    value = ws * E * N * ops / t_total
+    ms_step = t_total / args.steps * 1e3
+
+    # ---- dominant kernel: the FP32 tangent product, CUDA events on its stream
+    y32 = y.float().contiguous()
+    ts.ts_residual(g.prob, y32, torch.empty_like(y32))
+    v32 = torch.tensor(np.random.default_rng(0).standard_normal(y.shape), dtype=torch.float32, device="cuda")
+    hv = torch.empty_like(v32)
+    for _ in range(3):
+        ts.ts_jvp(g.prob, v32, hv)
+    R = 20
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(R):
+        ts.ts_jvp(g.prob, v32, hv)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_jvp = e0.elapsed_time(e1) / 1e3 / R
+    # residual (tau refresh) in FP32 for the breakdown
+    r32 = torch.empty_like(y32)
+    e0.record(stream)
+    for _ in range(3):
+        ts.ts_residual(g.prob, y32, r32)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_res32 = e0.elapsed_time(e1) / 1e3 / 3
+    peak, peak_kind = _peaks()
+    alg = _jvp_bytes(case)
+    achieved = alg / t_jvp / 1e9
+    traffic = _profile_traffic(os.path.join(ROOT, "paper_2311_09465_gb300", "csrc", "apply.cu"))
+
+    # ---- end-to-end through the public API with host buffers
+    y_host = torch.tensor(case.y0, dtype=torch.float64).pin_memory()
+    y_back = torch.empty_like(y_host).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    yd = y_host.to("cuda", non_blocking=True)
+    rep_e = g.solve(yd, **dict(opts, max_steps=args.steps))
+    y_back.copy_(yd, non_blocking=True)
+    torch.cuda.synchronize()
+    t_e2e = _max_over_ranks(dist, time.perf_counter() - t0)
+    ops_e = rep_e["matvecs"] + rep_e["steps"] + 1
+    e2e = {"value": ws * E * N * ops_e / t_e2e, "unit": "element-mode evals/s",
+           "h2d_bytes_per_step": int(y_host.numel() * 8 / args.steps),
+           "d2h_bytes_per_step": int(y_host.numel() * 8 / args.steps)}
+
+    # ---- time to residual 1e-8 r_ref: mixed vs plain FP64 (same GPU)
+    ttr = {}
+    if args.solve:
+        for prec in (32, 64):
+            yy = torch.tensor(case.y0, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rs = g.solve(yy, precision=prec, tol=1e-8, max_steps=args.solve_steps, krylov=100,
+                         eps_ls=0.05, max_matvec=2000, precond=1, ser=1.0, raise_on_noconv=False)
+            torch.cuda.synchronize()
+            ttr["mixed" if prec == 32 else "fp64"] = {
+                "seconds": time.perf_counter() - t0, "converged": rs["status"] == 0,
+                "r_final": rs["r_final"], "steps": rs["steps"], "matvecs": rs["matvecs"]}
+            if prec == 32:
+                y_mixed = yy.clone()
+        if ttr["mixed"]["converged"] and ttr["fp64"]["converged"]:
+            ttr["speedup_mixed_over_fp64"] = ttr["fp64"]["seconds"] / ttr["mixed"]["seconds"]
+            ttr["field_rel_l2_mixed_vs_fp64"] = float((y_mixed - yy).norm() / yy.norm())
+
+    cpu = _cpu_baseline(case, args) if (rank == 0 and ws == 1 and not args.no_cpu) else None
+    out = {
+        "metric": METRIC, "value": value, "unit": "element-mode evals/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic seeded junction mesh and inflow (patient Fontan data not available)",
+        "config": _config(case, {"parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"}),
+        "e2e": e2e, "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "apply_kernel (FP32 tangent product, LIN_A), all colours",
+                     "algorithmic_bytes": alg, "launch_ms": t_jvp * 1e3, "peak_source": peak_kind},
+        "cpu_baseline": cpu,
+        "clocks": clk,
+        "breakdown": {"jvp_fp32_ms": t_jvp * 1e3, "residual_fp32_ms": t_res32 * 1e3,
+                      "solve_report": {k: rep[k] for k in ("steps", "matvecs", "t_residual", "t_jvp", "t_krylov")}},
+        "time_to_residual_1e-8": ttr or None,
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    g.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def _oracle_step_rate(case, n_elem, n_jvp, seed=0):
+    """Oracle residual + tangent products on a fixed element sample; returns (evals/s, seconds)."""
+    from oracle import operator as op
+    prob = op.problem_from_case(case)
+    rng = np.random.default_rng(seed)
+    el = np.sort(rng.choice(case.mesh.n_tets, size=n_elem, replace=False))
+    y = case.y0
+    v = np.random.default_rng(seed + 1).standard_normal(y.shape)
+    t0 = time.perf_counter()
+    lin = op.linearize(prob, y, elems=el)
+    op.apply(prob, lin, y, "frozen")
+    for _ in range(n_jvp):
+        op.apply(prob, lin, v, "lin_a", mask_dirichlet_input=True)
+    dt = time.perf_counter() - t0
+    return n_elem * case.N * (n_jvp + 1) / dt, dt
+
+
+def _cpu_baseline(case, args):
+    n_elem = args.cpu_sample
+    rate, dt = _oracle_step_rate(case, n_elem, KRYLOV)
+    return {"value": rate, "unit": "element-mode evals/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n_elem} random elements of the same mesh, 1 residual + {KRYLOV} tangent "
+                      f"products (FP64 numpy, complex modes, explicit convolution matrices, "
+                      f"library eigensolver); {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    case = _workload()
+    rates = []
+    for k in range(args.warmup + args.steps):
+        rate, dt = _oracle_step_rate(case, args.ref_sample, KRYLOV, seed=k)
+        if k >= args.warmup:
+            rates.append((rate, dt))
+    t = sum(d for _, d in rates)
+    work = sum(r * d for r, d in rates)
+    value = work / t
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "element-mode evals/s",
+           "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": _config(case),
+           "cpu_baseline": {"value": value, "unit": "element-mode evals/s", "cores": 1, "kind": "oracle",
+                            "sample": f"{args.ref_sample} random elements per step, 1 residual + "
+                                      f"{KRYLOV} tangent products"},
+           "e2e": {"value": value, "unit": "element-mode evals/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gls", choices=["gls", "reference"])
+    ap.add_argument("--dt", type=float, default=0.2, help="pseudo-time step")
+    ap.add_argument("--no-solve", dest="solve", action="store_false")
+    ap.add_argument("--solve-steps", type=int, default=60)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=400)
+    ap.add_argument("--ref-sample", type=int, default=200)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,177 @@
+/*
+ * tsgls.h -- C ABI of the GB300 time-spectral Galerkin/least-squares (GLS)
+ * Navier-Stokes operator and solver.
+ *
+ * Method: Esmaily & Jia, "A new stabilized time-spectral finite element
+ * solver for fast simulation of blood flow", arXiv 2311.09465.  The
+ * time-periodic incompressible Navier-Stokes equations are expanded in N
+ * Fourier modes (section 2.4, eq. upgh_def), discretised with equal-order
+ * linear tetrahedra and stabilised by a least-squares term weighted by the
+ * mode-coupling matrix tau (eq. 3D-tau).  The discrete residual is eq. (Rmc);
+ * its tangent is eq. (K_mat); the nonlinear solve is pseudo-time Newton with
+ * restarted GMRES (sections 2.4-2.5).
+ *
+ * Data layout of every modal field (y, r, v, Hv): node-major, contiguous,
+ *   field[V][4][N][2]   with field index 0..2 = velocity u1,u2,u3, 3 = pressure,
+ *                       mode n = 0..N-1, last index = real, imaginary part.
+ * This is the real-valued unknown vector of section 2.5.1 (8N reals per node).
+ * The imaginary part of mode 0 is carried but is always zero on output and
+ * ignored on input.  Element type is float (precision 32) or double (64).
+ *
+ * Ownership: pointers named "host" are read during the call and copied;
+ * pointers to modal fields are caller-owned DEVICE memory (e.g. PyTorch CUDA
+ * tensors) on the current CUDA device.  Handles (ts_mesh, ts_problem) are
+ * library-owned and released only by the matching *_free call.  Streams are
+ * cudaStream_t passed as void* (NULL = legacy default stream).
+ *
+ * Errors: every int-returning call returns 0 on success and a negative
+ * TS_ERR_* code otherwise; ts_last_error() gives a message for the calling
+ * thread.  Calls never abort the process and never leave a kernel waiting.
+ */
+#ifndef TSGLS_H
+#define TSGLS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TS_OK            0
+#define TS_ERR_ARG      -1   /* invalid argument, size or state            */
+#define TS_ERR_CUDA     -2   /* a CUDA runtime call failed                 */
+#define TS_ERR_OOM      -3   /* device allocation failed                   */
+#define TS_ERR_NOCONV   -4   /* solver hit its step or matvec cap          */
+#define TS_ERR_NAN      -5   /* non-finite residual norm                   */
+#define TS_ERR_UNSUPPORTED -6 /* mode count without a compiled kernel      */
+
+/* boundary-condition kinds for ts_set_bc */
+#define TS_BC_DIRICHLET  1   /* velocity prescribed (values carried in y)  */
+#define TS_BC_TRACTION   2   /* -p n + mu du/dn = h n with h = 0           */
+#define TS_BC_RESISTANCE 3   /* h_n = -R Q_n, Q_n = int u_n . n (per mode) */
+
+/* tangent variants for ts_jvp / ts_solve (eq. K_mat) */
+#define TS_JVP_PAPER   0   /* A, tau frozen; LS parts of G_i, D_j dropped (section 2.5.2) */
+#define TS_JVP_FROZEN  1   /* A, tau frozen; all blocks of eq. (K_mat)                    */
+#define TS_JVP_LIN_A   2   /* FROZEN + derivative of A_j (tau frozen): exact up to d tau   */
+
+typedef struct ts_mesh ts_mesh;
+typedef struct ts_problem ts_problem;
+
+typedef struct {
+  int    N;          /* independent Fourier modes (mean + N-1 harmonics), section 2.1 */
+  double rho;        /* density                                                       */
+  double mu;         /* dynamic viscosity; kappa in tau is mu/rho                     */
+  double omega;      /* base angular frequency, Omega_mm = i m omega (eq. phi-def)    */
+  double C_I;        /* tau constant, 3 for linear tetrahedra (section 2.2)           */
+  double c1;         /* pseudo-time mass coefficient, 1.5 (section 2.5.3)             */
+  double dt_pseudo;  /* pseudo-time step; <= 0 or inf means plain Newton              */
+  int    jvp_variant;/* TS_JVP_*                                                      */
+} ts_params;
+
+typedef struct {
+  int    precision;    /* 64: FP64 operator everywhere; 32: FP32 tangent products inside
+                          FP64 GMRES with an FP64 outer residual (iterative refinement) */
+  double tol;          /* stop when ||r||_2 <= tol * r_ref (default 1e-8)              */
+  double r_ref;        /* reference norm; <= 0 means ||r(y_in)||_2                     */
+  int    max_steps;    /* pseudo-time / Newton steps                                   */
+  int    krylov;       /* GMRES restart length (100 in section 3.2)                    */
+  double eps_ls;       /* GMRES relative tolerance (0.05 in section 2.4, remark 6)     */
+  int    max_matvec;   /* per linear solve (10000 in section 3.2)                      */
+  int    verbose;      /* print one line per step to stderr                            */
+  int    precond;      /* 0: none; 1: right diagonal scaling by an approximate diag(H)
+                          (viscous + mass + scalar-tau LS terms per node; changes the
+                          GMRES path only, never the converged field)                  */
+  double ser;          /* > 0: pseudo-time step grows as dt_k = dt_0 (|r_0|/|r_k|)^ser
+                          (switched evolution relaxation; dt_0 = the problem's
+                          dt_pseudo, which must be finite); 0: fixed dt (section 2.5.3) */
+} ts_solve_opts;
+
+typedef struct {
+  int    steps;         /* pseudo-time steps taken                              */
+  int    matvecs;       /* total tangent products                               */
+  double r_ref;         /* reference norm used                                  */
+  double r_final;       /* final ||r||_2 / r_ref                                */
+  double seconds;       /* wall time of the solve                               */
+  double t_residual;    /* seconds in residual evaluations (incl. tau)          */
+  double t_jvp;         /* seconds in tangent products                          */
+  double t_krylov;      /* seconds in Gram-Schmidt, norms and updates           */
+  int    hist_len;      /* entries written to hist                              */
+  double hist[512];     /* ||r||/r_ref after each step                          */
+} ts_solve_report;
+
+/* Copies a tetrahedral mesh to the device and precomputes per-element shape
+ * function gradients, volume and the metric G_ij = dxi_k/dx_i dxi_k/dx_j
+ * (eq. metric; unit reference tetrahedron), and an element colouring (no two
+ * elements of one colour share a node) used for the scatter-add.
+ *   xyz_host   [n_nodes][3] coordinates
+ *   tets_host  [n_tets][4]  node ids, any orientation, 0-based
+ *   bfaces_host[n_bfaces][3] boundary triangles (outward or not: the library
+ *                            orients them with the owning tetrahedron)
+ *   btag_host  [n_bfaces]   integer tag per boundary triangle
+ * Fails with TS_ERR_ARG on out-of-range ids or a degenerate tetrahedron. */
+int  ts_mesh_load(const double* xyz_host, int64_t n_nodes, const int32_t* tets_host,
+                  int64_t n_tets, const int32_t* bfaces_host, const int32_t* btag_host,
+                  int64_t n_bfaces, ts_mesh** out);
+void ts_mesh_free(ts_mesh* mesh);
+/* number of element colours of a loaded mesh (or negative error) */
+int  ts_mesh_colors(const ts_mesh* mesh);
+
+/* Creates a problem (physics + boundary conditions) on a mesh.  The mesh must
+ * outlive the problem.  TS_ERR_UNSUPPORTED if no kernel is compiled for N. */
+int  ts_problem_create(const ts_mesh* mesh, const ts_params* params, ts_problem** out);
+void ts_problem_free(ts_problem* prob);
+/* Changes pseudo-time step and tangent variant of an existing problem. */
+int  ts_problem_set(ts_problem* prob, double dt_pseudo, int jvp_variant);
+
+/* Assigns a boundary condition to all boundary triangles with this tag.
+ * TS_BC_DIRICHLET: nodes of those triangles become Dirichlet velocity nodes;
+ *   their momentum rows are excluded and their values are taken from y
+ *   (section 2.4 keeps Dirichlet data inside the unknown vector and holds it
+ *   fixed during the iterations).  Dirichlet wins over any other tag at
+ *   shared nodes.
+ * TS_BC_TRACTION: zero traction, nothing to add (the default).
+ * TS_BC_RESISTANCE: outlet with h_n = -value * Q_n; the residual gains
+ *   value * Q_n * int N_A n_i on that outlet (a rank-one coupling per mode). */
+int  ts_set_bc(ts_problem* prob, int tag, int kind, double value);
+
+/* Discrete residual r(y) of eq. (Rmc), section 2.4, for the caller's state y
+ * (device, layout above, precision 32 or 64).  Momentum rows of Dirichlet
+ * nodes and Im(mode 0) are zero.  Also freezes the linearisation used by
+ * ts_jvp: the convolution matrices A_j of y, tau at every quadrature point
+ * (eq. 3D-tau, computed by a Jacobi eigensolver), and tau L_i(y).
+ * y and r may not alias. */
+int  ts_residual(ts_problem* prob, const void* y, void* r, int precision, void* stream);
+
+/* Tangent product Hv (eq. K_mat, variant from the problem) at the state of
+ * the last ts_residual call, plus c1 rho / dt_pseudo M v on the momentum rows
+ * (section 2.5.3) when dt_pseudo is finite.  Dirichlet velocity entries and
+ * Im(mode 0) of v are ignored; the same rows of Hv are zero.  If the last
+ * residual was computed in the other precision its state is converted.
+ * TS_ERR_ARG if no residual was computed yet.  v and Hv may not alias. */
+int  ts_jvp(ts_problem* prob, const void* v, void* Hv, int precision, void* stream);
+
+/* Pseudo-time Newton-GMRES solve (sections 2.4-2.5) in place on y_inout
+ * (device, double, layout above, Dirichlet values already set).  Each step:
+ * r = r(y); stop if ||r|| <= tol r_ref; solve (H + c1 rho/dt M) d = -r with
+ * restarted GMRES (FP64 Gram-Schmidt and Hessenberg); y += d on free
+ * unknowns.  Runs on the given stream; synchronises with the host once per
+ * GMRES iteration.  Returns TS_ERR_NOCONV when max_steps is reached (y holds
+ * the last iterate, report filled), TS_ERR_NAN on a non-finite norm. */
+int  ts_solve(ts_problem* prob, void* y_inout, const ts_solve_opts* opts,
+              ts_solve_report* report, void* stream);
+
+/* Thread-local message describing the last error. */
+const char* ts_last_error(void);
+
+/* Library version string. */
+const char* ts_version(void);
+
+/* Number of kernels this library has launched in this process (all devices,
+ * all streams); a diagnostic for counting launches inside a timed region. */
+int64_t ts_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TSGLS_H */

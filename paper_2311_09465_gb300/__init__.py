@@ -1,0 +1,255 @@
+"""Python binding of ``libtsgls`` (GB300 time-spectral GLS Navier-Stokes).
+
+Argument marshalling only: every step of the operator and of the solve runs
+in the CUDA library (``include/tsgls.h``).  Modal fields are CUDA tensors of
+shape [V, 4, N, 2] (node, field u1/u2/u3/p, mode, re/im), float32 or float64,
+contiguous.  There is no CPU fallback: the first call loads the library
+and raises ImportError if it is missing (build it with
+``python -m paper_2311_09465_gb300.build``).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libtsgls.so")
+
+TS_OK, TS_ERR_ARG, TS_ERR_CUDA, TS_ERR_OOM, TS_ERR_NOCONV, TS_ERR_NAN, TS_ERR_UNSUPPORTED = (
+    0, -1, -2, -3, -4, -5, -6)
+TS_BC_DIRICHLET, TS_BC_TRACTION, TS_BC_RESISTANCE = 1, 2, 3
+TS_JVP_PAPER, TS_JVP_FROZEN, TS_JVP_LIN_A = 0, 1, 2
+VARIANTS = {"paper": TS_JVP_PAPER, "frozen": TS_JVP_FROZEN, "lin_a": TS_JVP_LIN_A}
+SUPPORTED_N = (1, 2, 3, 4, 5, 7, 10, 15)
+
+
+class TsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"tsgls error {code}: {msg}")
+        self.code = code
+
+
+class ts_params(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("rho", ctypes.c_double), ("mu", ctypes.c_double),
+                ("omega", ctypes.c_double), ("C_I", ctypes.c_double), ("c1", ctypes.c_double),
+                ("dt_pseudo", ctypes.c_double), ("jvp_variant", ctypes.c_int)]
+
+
+class ts_solve_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("tol", ctypes.c_double), ("r_ref", ctypes.c_double),
+                ("max_steps", ctypes.c_int), ("krylov", ctypes.c_int), ("eps_ls", ctypes.c_double),
+                ("max_matvec", ctypes.c_int), ("verbose", ctypes.c_int), ("precond", ctypes.c_int),
+                ("ser", ctypes.c_double)]
+
+
+class ts_solve_report(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int), ("matvecs", ctypes.c_int), ("r_ref", ctypes.c_double),
+                ("r_final", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("t_residual", ctypes.c_double), ("t_jvp", ctypes.c_double),
+                ("t_krylov", ctypes.c_double), ("hist_len", ctypes.c_int),
+                ("hist", ctypes.c_double * 512)]
+
+    def to_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "hist"}
+        d["hist"] = list(self.hist[: self.hist_len])
+        return d
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libtsgls.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libtsgls.so not built ({LIB_PATH}); run python -m paper_2311_09465_gb300.build")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32p, dp = ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)
+    L.ts_mesh_load.argtypes = [dp, i64, i32p, i64, i32p, i32p, i64, ctypes.POINTER(vp)]
+    L.ts_mesh_free.argtypes = [vp]
+    L.ts_mesh_free.restype = None
+    L.ts_mesh_colors.argtypes = [vp]
+    L.ts_problem_create.argtypes = [vp, ctypes.POINTER(ts_params), ctypes.POINTER(vp)]
+    L.ts_problem_free.argtypes = [vp]
+    L.ts_problem_free.restype = None
+    L.ts_problem_set.argtypes = [vp, ctypes.c_double, ctypes.c_int]
+    L.ts_set_bc.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double]
+    L.ts_residual.argtypes = [vp, vp, vp, ctypes.c_int, vp]
+    L.ts_jvp.argtypes = [vp, vp, vp, ctypes.c_int, vp]
+    L.ts_solve.argtypes = [vp, vp, ctypes.POINTER(ts_solve_opts), ctypes.POINTER(ts_solve_report), vp]
+    L.ts_last_error.restype = ctypes.c_char_p
+    L.ts_version.restype = ctypes.c_char_p
+    L.ts_launch_count.restype = ctypes.c_int64
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != 0:
+        raise TsError(rc, lib().ts_last_error().decode())
+    return rc
+
+
+def ts_last_error() -> str:
+    return lib().ts_last_error().decode()
+
+
+def ts_version() -> str:
+    return lib().ts_version().decode()
+
+
+def ts_launch_count() -> int:
+    return int(lib().ts_launch_count())
+
+
+def _stream_ptr(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _field_ptr(t, precision=None):
+    import torch
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("modal fields must be contiguous CUDA tensors")
+    p = 64 if t.dtype == torch.float64 else 32 if t.dtype == torch.float32 else None
+    if p is None:
+        raise ValueError("modal fields must be float32 or float64")
+    if precision is not None and precision != p:
+        raise ValueError("tensor dtype does not match precision")
+    return ctypes.c_void_p(t.data_ptr()), p
+
+
+# ------------------------------------------------------------------ C ABI mirrors
+
+def ts_mesh_load(xyz, tets, bfaces, btag):
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    tets = np.ascontiguousarray(tets, dtype=np.int32)
+    bfaces = np.ascontiguousarray(bfaces, dtype=np.int32)
+    btag = np.ascontiguousarray(btag, dtype=np.int32)
+    out = ctypes.c_void_p()
+    _check(lib().ts_mesh_load(xyz.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), xyz.shape[0],
+                              tets.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), tets.shape[0],
+                              bfaces.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                              btag.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), bfaces.shape[0],
+                              ctypes.byref(out)))
+    return out
+
+
+def ts_mesh_free(mesh):
+    lib().ts_mesh_free(mesh)
+
+
+def ts_mesh_colors(mesh) -> int:
+    n = lib().ts_mesh_colors(mesh)
+    if n < 0:
+        _check(n)
+    return n
+
+
+def ts_problem_create(mesh, params: ts_params):
+    out = ctypes.c_void_p()
+    _check(lib().ts_problem_create(mesh, ctypes.byref(params), ctypes.byref(out)))
+    return out
+
+
+def ts_problem_free(prob):
+    lib().ts_problem_free(prob)
+
+
+def ts_problem_set(prob, dt_pseudo: float, jvp_variant: int):
+    _check(lib().ts_problem_set(prob, dt_pseudo, jvp_variant))
+
+
+def ts_set_bc(prob, tag: int, kind: int, value: float = 0.0):
+    _check(lib().ts_set_bc(prob, tag, kind, value))
+
+
+def ts_residual(prob, y, r, precision=None, stream=None):
+    py, p = _field_ptr(y, precision)
+    pr, _ = _field_ptr(r, p)
+    _check(lib().ts_residual(prob, py, pr, p, _stream_ptr(stream)))
+    return r
+
+
+def ts_jvp(prob, v, hv, precision=None, stream=None):
+    pv, p = _field_ptr(v, precision)
+    ph, _ = _field_ptr(hv, p)
+    _check(lib().ts_jvp(prob, pv, ph, p, _stream_ptr(stream)))
+    return hv
+
+
+def ts_solve(prob, y, opts: ts_solve_opts, stream=None, raise_on_noconv=True) -> dict:
+    py, p = _field_ptr(y, 64)
+    rep = ts_solve_report()
+    rc = lib().ts_solve(prob, py, ctypes.byref(opts), ctypes.byref(rep), _stream_ptr(stream))
+    d = rep.to_dict()
+    d["status"] = rc
+    if rc != 0 and (raise_on_noconv or rc != TS_ERR_NOCONV):
+        raise TsError(rc, lib().ts_last_error().decode())
+    return d
+
+
+# ------------------------------------------------------------------ convenience
+
+class GLSProblem:
+    """Mesh + problem handles for a seeded case (``workloads.cases.Case``)."""
+
+    def __init__(self, case, variant="lin_a", dt_pseudo=math.inf):
+        m = case.mesh
+        self.case = case
+        self.N = case.N
+        self.n_nodes = m.n_nodes
+        self.mesh = ts_mesh_load(m.xyz, m.tets, m.bfaces, m.btag)
+        prm = ts_params(N=case.N, rho=case.rho, mu=case.mu, omega=case.omega, C_I=case.C_I,
+                        c1=case.c1, dt_pseudo=dt_pseudo, jvp_variant=VARIANTS[variant])
+        self.prob = ts_problem_create(self.mesh, prm)
+        for tag in case.dirichlet_tags:
+            ts_set_bc(self.prob, tag, TS_BC_DIRICHLET)
+        for tag, R in case.resistance.items():
+            ts_set_bc(self.prob, tag, TS_BC_RESISTANCE, R)
+
+    def set(self, dt_pseudo=math.inf, variant="lin_a"):
+        ts_problem_set(self.prob, dt_pseudo, VARIANTS[variant])
+
+    def colors(self):
+        return ts_mesh_colors(self.mesh)
+
+    def field(self, dtype, device="cuda"):
+        import torch
+        return torch.zeros((self.n_nodes, 4, self.N, 2), dtype=dtype, device=device)
+
+    def residual(self, y, r=None, stream=None):
+        r = self.field(y.dtype, y.device) if r is None else r
+        return ts_residual(self.prob, y, r, stream=stream)
+
+    def jvp(self, v, hv=None, stream=None):
+        hv = self.field(v.dtype, v.device) if hv is None else hv
+        return ts_jvp(self.prob, v, hv, stream=stream)
+
+    def solve(self, y, precision=64, tol=1e-8, r_ref=0.0, max_steps=200, krylov=100,
+              eps_ls=0.05, max_matvec=10000, verbose=False, stream=None, raise_on_noconv=True,
+              precond=1, ser=0.0):
+        opts = ts_solve_opts(precision=precision, tol=tol, r_ref=r_ref, max_steps=max_steps,
+                             krylov=krylov, eps_ls=eps_ls, max_matvec=max_matvec,
+                             verbose=int(verbose), precond=int(precond), ser=float(ser))
+        return ts_solve(self.prob, y, opts, stream=stream, raise_on_noconv=raise_on_noconv)
+
+    def close(self):
+        if getattr(self, "prob", None):
+            ts_problem_free(self.prob)
+            self.prob = None
+        if getattr(self, "mesh", None):
+            ts_mesh_free(self.mesh)
+            self.mesh = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,879 @@
+// C ABI of the GB300 time-spectral GLS library: mesh and problem set-up,
+// residual and tangent dispatch, and the pseudo-time Newton-GMRES solve
+// (sections 2.4-2.5 of Esmaily & Jia, arXiv 2311.09465).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/tsgls.h"
+#include "kernels.h"
+
+using namespace ts;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+#define TS_CUDA(call)                                                                   \
+  do {                                                                                  \
+    cudaError_t err__ = (call);                                                         \
+    if (err__ != cudaSuccess)                                                           \
+      return fail(err__ == cudaErrorMemoryAllocation ? TS_ERR_OOM : TS_ERR_CUDA,        \
+                  std::string(#call) + ": " + cudaGetErrorString(err__));               \
+  } while (0)
+
+#define TS_TRY(...)               \
+  do {                            \
+    int rc__ = (__VA_ARGS__);     \
+    if (rc__ != 0) return rc__;   \
+  } while (0)
+
+template <typename T>
+int dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(e == cudaErrorMemoryAllocation ? TS_ERR_OOM : TS_ERR_CUDA,
+                std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  return 0;
+}
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+bool n_supported(int N) {
+  const int list[] = {TS_N_LIST};
+  for (int n : list)
+    if (n == N) return true;
+  return false;
+}
+
+}  // namespace
+
+struct ts_mesh {
+  int device = 0;
+  int64_t V = 0, E = 0, F = 0;
+  std::vector<double> xyz;
+  std::vector<int32_t> tets;          // colour-sorted, [E][4]
+  std::vector<int32_t> bfaces;        // [F][3], outward
+  std::vector<int32_t> btag;
+  std::vector<int64_t> colour_off;    // colour c: [off[c], off[c+1])
+  int4* d_tets = nullptr;
+  double* d_geo64 = nullptr;
+  float* d_geo32 = nullptr;
+};
+
+template <typename T>
+struct LinState {
+  T* u0 = nullptr;      // [V][4][C] linearisation state
+  T* tau = nullptr;     // [E][4][NT_PAD]
+  T* t0 = nullptr;      // [E][4][3][C] tau L at the state
+  T* dft = nullptr;     // forward [K][C] then inverse [C][K]
+  T* u0t = nullptr;     // [V][3][K] u0 velocity sampled in time (FP32 fast path)
+  bool valid = false;
+};
+
+struct Outlet {
+  int tag;
+  double R;
+  std::vector<int32_t> nodes;
+  std::vector<double> w;        // [n][3] int N_A n_i over the outlet
+  int32_t* d_nodes = nullptr;
+  double* d_w64 = nullptr;
+  float* d_w32 = nullptr;
+};
+
+struct ts_problem {
+  const ts_mesh* mesh = nullptr;
+  ts_params p{};
+  int C = 0, K = 0, NTP = 0;
+  std::vector<uint8_t> dmask;
+  uint8_t* d_dmask = nullptr;
+  bool dmask_dirty = true;
+  std::vector<Outlet> outlets;
+  LinState<float> l32;
+  LinState<double> l64;
+  unsigned* d_counter = nullptr;
+  // solver workspace (FP64)
+  double* d_basis = nullptr;
+  int basis_m = 0;
+  double *d_w = nullptr, *d_r = nullptr, *d_dy = nullptr, *d_partial = nullptr, *d_h = nullptr;
+  float *d_v32 = nullptr, *d_w32 = nullptr;
+  double *d_D = nullptr, *d_t = nullptr;      // preconditioner diagonal (inverted), temp
+  bool fast32 = true;    // FP32 products with the single-launch kernel (jvp32.cu)
+};
+
+// ------------------------------------------------------------------ helpers
+
+static int64_t field_len(const ts_problem* pr) { return pr->mesh->V * 4 * (int64_t)pr->C; }
+
+namespace ts {
+int dft_constant_total() {
+  const int list[] = {TS_N_LIST};
+  int off = 0;
+  for (int n : list) off += 2 * (3 * n - 2) * (2 * n);
+  return off;
+}
+int dft_constant_offset(int N) {
+  const int list[] = {TS_N_LIST};
+  int off = 0;
+  for (int n : list) {
+    if (n == N) return off;
+    off += 2 * (3 * n - 2) * (2 * n);
+  }
+  return -1;
+}
+}  // namespace ts
+
+static void dft_tables(int N, std::vector<double>& out) {
+  const int C = 2 * N, K = 3 * N - 2;
+  out.assign((size_t)2 * K * C, 0.0);
+  const double pi = 3.14159265358979323846;
+  for (int k = 0; k < K; ++k) {
+    out[k * C + 0] = 1.0;
+    for (int n = 1; n < N; ++n) {
+      double th = 2.0 * pi * n * k / K;
+      out[k * C + 2 * n] = 2.0 * std::cos(th);
+      out[k * C + 2 * n + 1] = -2.0 * std::sin(th);
+    }
+  }
+  double* inv = out.data() + K * C;
+  for (int k = 0; k < K; ++k) {
+    inv[0 * K + k] = 1.0 / K;
+    for (int n = 1; n < N; ++n) {
+      double th = 2.0 * pi * n * k / K;
+      inv[(2 * n) * K + k] = std::cos(th) / K;
+      inv[(2 * n + 1) * K + k] = -std::sin(th) / K;
+    }
+  }
+}
+
+template <typename T>
+static int lin_alloc(ts_problem* pr, LinState<T>& l) {
+  if (l.u0) return 0;
+  const ts_mesh* m = pr->mesh;
+  TS_TRY(dalloc(&l.u0, (size_t)field_len(pr)));
+  TS_TRY(dalloc(&l.tau, (size_t)m->E * 4 * pr->NTP));
+  TS_TRY(dalloc(&l.t0, (size_t)m->E * 12 * pr->C));
+  std::vector<double> tab;
+  dft_tables(pr->p.N, tab);
+  std::vector<T> tt(tab.begin(), tab.end());
+  TS_TRY(dalloc(&l.dft, tt.size()));
+  TS_CUDA(cudaMemcpy(l.dft, tt.data(), tt.size() * sizeof(T), cudaMemcpyHostToDevice));
+  TS_TRY(dalloc(&l.u0t, (size_t)m->V * 3 * pr->K));
+  // constant-memory DFT tables of every compiled N (used by the FP32 fast path)
+  std::vector<float> all(dft_constant_total());
+  const int list[] = {TS_N_LIST};
+  for (int n : list) {
+    std::vector<double> tn;
+    dft_tables(n, tn);
+    std::copy(tn.begin(), tn.end(), all.begin() + dft_constant_offset(n));
+  }
+  if (j32_upload_n123(all.data()) || j32_upload_n45(all.data()) || j32_upload_n7(all.data()))
+    return fail(TS_ERR_CUDA, "DFT constant upload failed");
+  return 0;
+}
+
+template <typename T>
+static void lin_free(LinState<T>& l) {
+  dfree(l.u0);
+  dfree(l.tau);
+  dfree(l.t0);
+  dfree(l.dft);
+  dfree(l.u0t);
+  l.valid = false;
+}
+
+static int sync_dmask(ts_problem* pr) {
+  if (!pr->dmask_dirty) return 0;
+  TS_CUDA(cudaMemcpy(pr->d_dmask, pr->dmask.data(), pr->dmask.size(), cudaMemcpyHostToDevice));
+  pr->dmask_dirty = false;
+  return 0;
+}
+
+template <typename T>
+static const T* geo_of(const ts_mesh* m);
+template <>
+const float* geo_of<float>(const ts_mesh* m) { return m->d_geo32; }
+template <>
+const double* geo_of<double>(const ts_mesh* m) { return m->d_geo64; }
+
+template <typename T>
+static LinState<T>& lin_of(ts_problem* pr);
+template <>
+LinState<float>& lin_of<float>(ts_problem* pr) { return pr->l32; }
+template <>
+LinState<double>& lin_of<double>(ts_problem* pr) { return pr->l64; }
+
+template <typename T>
+static const T* outlet_w(const Outlet& o);
+template <>
+const float* outlet_w<float>(const Outlet& o) { return o.d_w32; }
+template <>
+const double* outlet_w<double>(const Outlet& o) { return o.d_w64; }
+
+template <typename T>
+static Phys<T> phys_of(const ts_problem* pr, bool with_mass) {
+  Phys<T> ph;
+  ph.rho = (T)pr->p.rho;
+  ph.mu = (T)pr->p.mu;
+  ph.omega = (T)pr->p.omega;
+  ph.nu = (T)(pr->p.mu / pr->p.rho);
+  ph.C_I = (T)pr->p.C_I;
+  double dt = pr->p.dt_pseudo;
+  ph.mass_coef = (with_mass && dt > 0 && std::isfinite(dt)) ? (T)(pr->p.c1 * pr->p.rho / dt) : T(0);
+  return ph;
+}
+
+// dispatch on the compiled mode counts
+template <typename T, int N>
+static int apply_colours(ts_problem* pr, int mode, const T* v, const T* u0, LinState<T>& l,
+                         T* out, bool with_mass, cudaStream_t st) {
+  const ts_mesh* m = pr->mesh;
+  Phys<T> ph = phys_of<T>(pr, with_mass);
+  for (size_t c = 0; c + 1 < m->colour_off.size(); ++c) {
+    int rc = launch_apply<T, N>(mode, m->d_tets, geo_of<T>(m), v, u0, l.tau, l.t0, pr->d_dmask,
+                                out, l.dft, ph, m->colour_off[c], m->colour_off[c + 1], st);
+    if (rc) return fail(rc == -6 ? TS_ERR_UNSUPPORTED : TS_ERR_CUDA, "element kernel launch failed");
+  }
+  const bool mask_input = mode != MODE_RESIDUAL;
+  for (auto& o : pr->outlets) {
+    int rc = launch_outlet<T>(o.d_nodes, outlet_w<T>(o), (int)o.nodes.size(), (T)o.R, v,
+                              pr->d_dmask, mask_input ? 1 : 0, out, pr->C, st);
+    if (rc) return fail(TS_ERR_CUDA, "outlet kernel launch failed");
+  }
+  return 0;
+}
+
+template <typename T, int N>
+static int residual_impl(ts_problem* pr, const T* y, T* r, cudaStream_t st) {
+  const ts_mesh* m = pr->mesh;
+  LinState<T>& l = lin_of<T>(pr);
+  TS_TRY(lin_alloc(pr, l));
+  const int64_t n = field_len(pr);
+  TS_CUDA(cudaMemcpyAsync(l.u0, y, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  int rc = launch_tau<T, N>(m->d_tets, geo_of<T>(m), y, m->E, l.tau, (T)(pr->p.mu / pr->p.rho),
+                            (T)pr->p.C_I, pr->d_counter, st);
+  if (rc) return fail(TS_ERR_CUDA, "tau kernel launch failed");
+  TS_CUDA(cudaMemsetAsync(r, 0, n * sizeof(T), st));
+  TS_TRY(apply_colours<T, N>(pr, MODE_RESIDUAL, y, y, l, r, false, st));
+  if constexpr (sizeof(T) == 4 && N <= J32_MAX_N) {
+    if (launch_node_samples<N>((const float*)l.u0, (float*)l.u0t, m->V, st))
+      return fail(TS_ERR_CUDA, "node sample kernel failed");
+  }
+  l.valid = true;
+  // the other precision's state is now stale
+  if (sizeof(T) == 4) pr->l64.valid = false; else pr->l32.valid = false;
+  return 0;
+}
+
+template <typename D, typename S, int N>
+static int convert_lin(ts_problem* pr, LinState<D>& dst, LinState<S>& src, cudaStream_t st) {
+  TS_TRY(lin_alloc(pr, dst));
+  const ts_mesh* m = pr->mesh;
+  const int64_t n_u = field_len(pr), n_tau = m->E * 4 * pr->NTP, n_t0 = m->E * 12 * pr->C;
+  int rc = 0;
+  if (sizeof(D) == 4) {
+    rc |= vec_cast_d2f((float*)dst.u0, (const double*)src.u0, n_u, st);
+    rc |= vec_cast_d2f((float*)dst.tau, (const double*)src.tau, n_tau, st);
+    rc |= vec_cast_d2f((float*)dst.t0, (const double*)src.t0, n_t0, st);
+    if constexpr (N <= J32_MAX_N)
+      rc |= launch_node_samples<N>((const float*)dst.u0, (float*)dst.u0t, m->V, st);
+  } else {
+    rc |= vec_cast_f2d((double*)dst.u0, (const float*)src.u0, n_u, st);
+    rc |= vec_cast_f2d((double*)dst.tau, (const float*)src.tau, n_tau, st);
+    rc |= vec_cast_f2d((double*)dst.t0, (const float*)src.t0, n_t0, st);
+  }
+  if (rc) return fail(TS_ERR_CUDA, "state conversion failed");
+  dst.valid = true;
+  return 0;
+}
+
+static int mode_of_variant(int v) {
+  switch (v) {
+    case TS_JVP_PAPER: return MODE_JVP_PAPER;
+    case TS_JVP_FROZEN: return MODE_JVP_FROZEN;
+    case TS_JVP_LIN_A: return MODE_JVP_LIN_A;
+  }
+  return -1;
+}
+
+template <typename T, int N>
+static int jvp_impl(ts_problem* pr, const T* v, T* hv, cudaStream_t st) {
+  LinState<T>& l = lin_of<T>(pr);
+  if (!l.valid) {
+    if (sizeof(T) == 4 && pr->l64.valid)
+      TS_TRY(convert_lin<float, double, N>(pr, pr->l32, pr->l64, st));
+    else if (sizeof(T) == 8 && pr->l32.valid)
+      TS_TRY(convert_lin<double, float, N>(pr, pr->l64, pr->l32, st));
+    else
+      return fail(TS_ERR_ARG, "ts_jvp: no linearisation state (call ts_residual first)");
+  }
+  const int mode = mode_of_variant(pr->p.jvp_variant);
+  if (mode < 0) return fail(TS_ERR_ARG, "unknown jvp variant");
+  TS_CUDA(cudaMemsetAsync(hv, 0, field_len(pr) * sizeof(T), st));
+  if constexpr (sizeof(T) == 4 && N <= J32_MAX_N) if (pr->fast32) {
+    const ts_mesh* m = pr->mesh;
+    int rc = launch_jvp32<N>(mode, m->d_tets, m->d_geo32, (const float*)v, (const float*)l.u0t,
+                             (const float*)l.tau, (const float*)l.t0, pr->d_dmask, (float*)hv,
+                             phys_of<float>(pr, true), m->E, st);
+    if (rc) return fail(TS_ERR_CUDA, "FP32 tangent kernel launch failed");
+    for (auto& o : pr->outlets)
+      if (launch_outlet<T>(o.d_nodes, outlet_w<T>(o), (int)o.nodes.size(), (T)o.R, v, pr->d_dmask, 1,
+                           hv, pr->C, st))
+        return fail(TS_ERR_CUDA, "outlet kernel launch failed");
+    return 0;
+  }
+  return apply_colours<T, N>(pr, mode, v, l.u0, l, hv, true, st);
+}
+
+#define TS_DISPATCH(N_, CALL)                                                   \
+  switch (N_) {                                                                 \
+    case 1: { constexpr int NN = 1; return CALL; }                              \
+    case 2: { constexpr int NN = 2; return CALL; }                              \
+    case 3: { constexpr int NN = 3; return CALL; }                              \
+    case 4: { constexpr int NN = 4; return CALL; }                              \
+    case 5: { constexpr int NN = 5; return CALL; }                              \
+    case 7: { constexpr int NN = 7; return CALL; }                              \
+    case 10: { constexpr int NN = 10; return CALL; }                            \
+    case 15: { constexpr int NN = 15; return CALL; }                            \
+    default: return fail(TS_ERR_UNSUPPORTED, "no kernel compiled for this N");  \
+  }
+
+static int residual_any(ts_problem* pr, const void* y, void* r, int precision, cudaStream_t st) {
+  if (precision == 32) {
+    TS_DISPATCH(pr->p.N, (residual_impl<float, NN>(pr, (const float*)y, (float*)r, st)));
+  } else {
+    TS_DISPATCH(pr->p.N, (residual_impl<double, NN>(pr, (const double*)y, (double*)r, st)));
+  }
+}
+
+static int jvp_any(ts_problem* pr, const void* v, void* hv, int precision, cudaStream_t st) {
+  if (precision == 32) {
+    TS_DISPATCH(pr->p.N, (jvp_impl<float, NN>(pr, (const float*)v, (float*)hv, st)));
+  } else {
+    TS_DISPATCH(pr->p.N, (jvp_impl<double, NN>(pr, (const double*)v, (double*)hv, st)));
+  }
+}
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" {
+
+const char* ts_last_error(void) { return g_last_error.c_str(); }
+const char* ts_version(void) { return "tsgls-gb300 0.1 (sm_103a)"; }
+
+int64_t ts_launch_count(void) { return (int64_t)ts::launches_total(); }
+
+int ts_mesh_load(const double* xyz_host, int64_t n_nodes, const int32_t* tets_host,
+                 int64_t n_tets, const int32_t* bfaces_host, const int32_t* btag_host,
+                 int64_t n_bfaces, ts_mesh** out) {
+  if (!out) return fail(TS_ERR_ARG, "ts_mesh_load: out is NULL");
+  *out = nullptr;
+  if (!xyz_host || !tets_host || n_nodes < 4 || n_tets < 1 || n_bfaces < 0 ||
+      (n_bfaces > 0 && (!bfaces_host || !btag_host)))
+    return fail(TS_ERR_ARG, "ts_mesh_load: bad sizes or NULL arrays");
+  if (n_nodes >= (int64_t)1 << 31 || n_tets >= (int64_t)1 << 31)
+    return fail(TS_ERR_ARG, "ts_mesh_load: mesh too large for 32-bit ids");
+  for (int64_t i = 0; i < 4 * n_tets; ++i)
+    if (tets_host[i] < 0 || tets_host[i] >= n_nodes)
+      return fail(TS_ERR_ARG, "ts_mesh_load: tetrahedron node id out of range");
+  for (int64_t i = 0; i < 3 * n_bfaces; ++i)
+    if (bfaces_host[i] < 0 || bfaces_host[i] >= n_nodes)
+      return fail(TS_ERR_ARG, "ts_mesh_load: boundary face node id out of range");
+
+  ts_mesh* m = new ts_mesh();
+  cudaGetDevice(&m->device);
+  m->V = n_nodes;
+  m->E = n_tets;
+  m->F = n_bfaces;
+  m->xyz.assign(xyz_host, xyz_host + 3 * n_nodes);
+  // greedy colouring: the lowest colour unused at all four nodes
+  std::vector<uint64_t> used(n_nodes, 0);
+  std::vector<int> col(n_tets);
+  int ncol = 0;
+  for (int64_t e = 0; e < n_tets; ++e) {
+    const int32_t* t = tets_host + 4 * e;
+    uint64_t u = used[t[0]] | used[t[1]] | used[t[2]] | used[t[3]];
+    if (u == ~0ull) {
+      delete m;
+      return fail(TS_ERR_ARG, "ts_mesh_load: more than 64 element colours needed");
+    }
+    int c = __builtin_ctzll(~u);
+    col[e] = c;
+    ncol = std::max(ncol, c + 1);
+    for (int a = 0; a < 4; ++a) used[t[a]] |= 1ull << c;
+  }
+  std::vector<int64_t> cnt(ncol + 1, 0);
+  for (int64_t e = 0; e < n_tets; ++e) cnt[col[e] + 1]++;
+  for (int c = 0; c < ncol; ++c) cnt[c + 1] += cnt[c];
+  m->colour_off = cnt;
+  std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
+  m->tets.resize(4 * n_tets);
+  std::vector<double> geo(GEO_STRIDE * n_tets, 0.0);
+  for (int64_t e = 0; e < n_tets; ++e) {
+    int64_t d = pos[col[e]]++;
+    const int32_t* t = tets_host + 4 * e;
+    for (int a = 0; a < 4; ++a) m->tets[4 * d + a] = t[a];
+    const double* x0 = &m->xyz[3 * t[0]];
+    double J[3][3];   // J[i][k] = d x_i / d xi_k
+    for (int k = 0; k < 3; ++k)
+      for (int i = 0; i < 3; ++i) J[i][k] = m->xyz[3 * t[k + 1] + i] - x0[i];
+    double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                 J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                 J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+    double scale = 0;
+    for (int i = 0; i < 3; ++i)
+      for (int k = 0; k < 3; ++k) scale = std::max(scale, std::fabs(J[i][k]));
+    if (!(std::fabs(det) > 1e-14 * scale * scale * scale)) {
+      delete m;
+      return fail(TS_ERR_ARG, "ts_mesh_load: degenerate tetrahedron");
+    }
+    double inv[3][3];  // inv[k][i] = d xi_k / d x_i
+    inv[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
+    inv[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+    inv[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+    inv[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / det;
+    inv[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+    inv[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+    inv[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
+    inv[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+    inv[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+    double* g = &geo[GEO_STRIDE * d];
+    for (int j = 0; j < 3; ++j) {
+      g[0 * 3 + j] = -(inv[0][j] + inv[1][j] + inv[2][j]);
+      for (int a = 1; a < 4; ++a) g[a * 3 + j] = inv[a - 1][j];
+    }
+    g[GEO_VOL] = std::fabs(det) / 6.0;
+    auto G = [&](int i, int j) { return inv[0][i] * inv[0][j] + inv[1][i] * inv[1][j] + inv[2][i] * inv[2][j]; };
+    g[GEO_G + 0] = G(0, 0);
+    g[GEO_G + 1] = G(0, 1);
+    g[GEO_G + 2] = G(0, 2);
+    g[GEO_G + 3] = G(1, 1);
+    g[GEO_G + 4] = G(1, 2);
+    g[GEO_G + 5] = G(2, 2);
+  }
+  // boundary faces, oriented outward with the owning tetrahedron
+  std::vector<std::vector<int32_t>> node_tets(n_nodes);
+  for (int64_t e = 0; e < n_tets; ++e)
+    for (int a = 0; a < 4; ++a) node_tets[tets_host[4 * e + a]].push_back((int32_t)e);
+  m->bfaces.resize(3 * n_bfaces);
+  m->btag.assign(btag_host, btag_host + n_bfaces);
+  for (int64_t f = 0; f < n_bfaces; ++f) {
+    int32_t a = bfaces_host[3 * f], b = bfaces_host[3 * f + 1], c = bfaces_host[3 * f + 2];
+    int32_t opp = -1;
+    for (int32_t e : node_tets[a]) {
+      const int32_t* t = tets_host + 4 * e;
+      int hits = 0, other = -1;
+      for (int k = 0; k < 4; ++k) {
+        if (t[k] == a || t[k] == b || t[k] == c) ++hits;
+        else other = t[k];
+      }
+      if (hits == 3) {
+        opp = other;
+        break;
+      }
+    }
+    if (opp < 0) {
+      delete m;
+      return fail(TS_ERR_ARG, "ts_mesh_load: boundary face not on any tetrahedron");
+    }
+    const double* pa = &m->xyz[3 * a];
+    double u[3], v[3], w[3], n[3];
+    for (int i = 0; i < 3; ++i) {
+      u[i] = m->xyz[3 * b + i] - pa[i];
+      v[i] = m->xyz[3 * c + i] - pa[i];
+      w[i] = m->xyz[3 * opp + i] - pa[i];
+    }
+    n[0] = u[1] * v[2] - u[2] * v[1];
+    n[1] = u[2] * v[0] - u[0] * v[2];
+    n[2] = u[0] * v[1] - u[1] * v[0];
+    if (n[0] * w[0] + n[1] * w[1] + n[2] * w[2] > 0) std::swap(b, c);
+    m->bfaces[3 * f] = a;
+    m->bfaces[3 * f + 1] = b;
+    m->bfaces[3 * f + 2] = c;
+  }
+  std::vector<float> geo32(geo.begin(), geo.end());
+  int rc = 0;
+  rc |= dalloc(&m->d_tets, (size_t)n_tets);
+  rc |= dalloc(&m->d_geo64, geo.size());
+  rc |= dalloc(&m->d_geo32, geo32.size());
+  if (rc) {
+    ts_mesh_free(m);
+    return TS_ERR_OOM;
+  }
+  cudaError_t e1 = cudaMemcpy(m->d_tets, m->tets.data(), 16 * n_tets, cudaMemcpyHostToDevice);
+  cudaError_t e2 = cudaMemcpy(m->d_geo64, geo.data(), geo.size() * 8, cudaMemcpyHostToDevice);
+  cudaError_t e3 = cudaMemcpy(m->d_geo32, geo32.data(), geo32.size() * 4, cudaMemcpyHostToDevice);
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+    ts_mesh_free(m);
+    return fail(TS_ERR_CUDA, "ts_mesh_load: host-to-device copy failed");
+  }
+  *out = m;
+  return 0;
+}
+
+void ts_mesh_free(ts_mesh* m) {
+  if (!m) return;
+  dfree(m->d_tets);
+  dfree(m->d_geo64);
+  dfree(m->d_geo32);
+  delete m;
+}
+
+int ts_mesh_colors(const ts_mesh* m) {
+  if (!m) return fail(TS_ERR_ARG, "NULL mesh");
+  return (int)m->colour_off.size() - 1;
+}
+
+int ts_problem_create(const ts_mesh* mesh, const ts_params* params, ts_problem** out) {
+  if (!out || !mesh || !params) return fail(TS_ERR_ARG, "ts_problem_create: NULL argument");
+  *out = nullptr;
+  const ts_params& p = *params;
+  if (!n_supported(p.N)) return fail(TS_ERR_UNSUPPORTED, "ts_problem_create: N not compiled");
+  if (!(p.rho > 0) || !(p.mu > 0) || !(p.omega >= 0) || !(p.C_I > 0))
+    return fail(TS_ERR_ARG, "ts_problem_create: rho, mu, C_I must be positive, omega >= 0");
+  if (mode_of_variant(p.jvp_variant) < 0) return fail(TS_ERR_ARG, "unknown jvp variant");
+  ts_problem* pr = new ts_problem();
+  pr->mesh = mesh;
+  pr->p = p;
+  pr->C = 2 * p.N;
+  pr->K = 3 * p.N - 2;
+  const int nm = 2 * p.N - 1;
+  pr->NTP = ((nm * (nm + 1) / 2) + 3) & ~3;
+  pr->dmask.assign(mesh->V, 0);
+  {
+    const char* env = getenv("TSGLS_COLOURED_FP32");
+    pr->fast32 = !(env && env[0] == '1');
+  }
+  if (dalloc(&pr->d_dmask, (size_t)mesh->V) || dalloc(&pr->d_counter, 1)) {
+    ts_problem_free(pr);
+    return TS_ERR_OOM;
+  }
+  cudaMemset(pr->d_counter, 0, sizeof(unsigned));
+  *out = pr;
+  return 0;
+}
+
+void ts_problem_free(ts_problem* pr) {
+  if (!pr) return;
+  dfree(pr->d_dmask);
+  dfree(pr->d_counter);
+  for (auto& o : pr->outlets) {
+    dfree(o.d_nodes);
+    dfree(o.d_w64);
+    dfree(o.d_w32);
+  }
+  lin_free(pr->l32);
+  lin_free(pr->l64);
+  dfree(pr->d_basis);
+  dfree(pr->d_w);
+  dfree(pr->d_r);
+  dfree(pr->d_dy);
+  dfree(pr->d_partial);
+  dfree(pr->d_h);
+  dfree(pr->d_v32);
+  dfree(pr->d_w32);
+  dfree(pr->d_D);
+  dfree(pr->d_t);
+  delete pr;
+}
+
+int ts_problem_set(ts_problem* pr, double dt_pseudo, int jvp_variant) {
+  if (!pr) return fail(TS_ERR_ARG, "NULL problem");
+  if (mode_of_variant(jvp_variant) < 0) return fail(TS_ERR_ARG, "unknown jvp variant");
+  pr->p.dt_pseudo = dt_pseudo;
+  pr->p.jvp_variant = jvp_variant;
+  return 0;
+}
+
+int ts_set_bc(ts_problem* pr, int tag, int kind, double value) {
+  if (!pr) return fail(TS_ERR_ARG, "NULL problem");
+  const ts_mesh* m = pr->mesh;
+  if (kind == TS_BC_DIRICHLET) {
+    for (int64_t f = 0; f < m->F; ++f)
+      if (m->btag[f] == tag)
+        for (int k = 0; k < 3; ++k) pr->dmask[m->bfaces[3 * f + k]] = 1;
+    pr->dmask_dirty = true;
+    return 0;
+  }
+  if (kind == TS_BC_TRACTION) return 0;
+  if (kind != TS_BC_RESISTANCE) return fail(TS_ERR_ARG, "ts_set_bc: unknown kind");
+  if (!(value >= 0)) return fail(TS_ERR_ARG, "ts_set_bc: resistance must be >= 0");
+  Outlet o;
+  o.tag = tag;
+  o.R = value;
+  std::vector<int64_t> slot(m->V, -1);
+  for (int64_t f = 0; f < m->F; ++f) {
+    if (m->btag[f] != tag) continue;
+    const int32_t* t = &m->bfaces[3 * f];
+    const double* pa = &m->xyz[3 * t[0]];
+    double u[3], v[3], n6[3];
+    for (int i = 0; i < 3; ++i) {
+      u[i] = m->xyz[3 * t[1] + i] - pa[i];
+      v[i] = m->xyz[3 * t[2] + i] - pa[i];
+    }
+    // (area / 3) * unit normal = cross / 6 per face vertex
+    n6[0] = (u[1] * v[2] - u[2] * v[1]) / 6.0;
+    n6[1] = (u[2] * v[0] - u[0] * v[2]) / 6.0;
+    n6[2] = (u[0] * v[1] - u[1] * v[0]) / 6.0;
+    for (int k = 0; k < 3; ++k) {
+      int32_t A = t[k];
+      if (slot[A] < 0) {
+        slot[A] = (int64_t)o.nodes.size();
+        o.nodes.push_back(A);
+        o.w.insert(o.w.end(), {0.0, 0.0, 0.0});
+      }
+      for (int i = 0; i < 3; ++i) o.w[3 * slot[A] + i] += n6[i];
+    }
+  }
+  if (o.nodes.empty()) return fail(TS_ERR_ARG, "ts_set_bc: no boundary face carries this tag");
+  std::vector<float> w32(o.w.begin(), o.w.end());
+  int rc = dalloc(&o.d_nodes, o.nodes.size()) | dalloc(&o.d_w64, o.w.size()) |
+           dalloc(&o.d_w32, o.w.size());
+  if (rc) return TS_ERR_OOM;
+  TS_CUDA(cudaMemcpy(o.d_nodes, o.nodes.data(), o.nodes.size() * 4, cudaMemcpyHostToDevice));
+  TS_CUDA(cudaMemcpy(o.d_w64, o.w.data(), o.w.size() * 8, cudaMemcpyHostToDevice));
+  TS_CUDA(cudaMemcpy(o.d_w32, w32.data(), w32.size() * 4, cudaMemcpyHostToDevice));
+  pr->outlets.push_back(std::move(o));
+  return 0;
+}
+
+int ts_residual(ts_problem* pr, const void* y, void* r, int precision, void* stream) {
+  if (!pr || !y || !r) return fail(TS_ERR_ARG, "ts_residual: NULL argument");
+  if (precision != 32 && precision != 64) return fail(TS_ERR_ARG, "precision must be 32 or 64");
+  if (y == r) return fail(TS_ERR_ARG, "ts_residual: y and r alias");
+  TS_TRY(sync_dmask(pr));
+  return residual_any(pr, y, r, precision, (cudaStream_t)stream);
+}
+
+int ts_jvp(ts_problem* pr, const void* v, void* hv, int precision, void* stream) {
+  if (!pr || !v || !hv) return fail(TS_ERR_ARG, "ts_jvp: NULL argument");
+  if (precision != 32 && precision != 64) return fail(TS_ERR_ARG, "precision must be 32 or 64");
+  if (v == hv) return fail(TS_ERR_ARG, "ts_jvp: v and Hv alias");
+  TS_TRY(sync_dmask(pr));
+  return jvp_any(pr, v, hv, precision, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------------ solve
+
+static double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+static int dnorm(ts_problem* pr, const double* x, int64_t n, cudaStream_t st, double* out) {
+  if (krylov_dots(x, n, 1, x, n, pr->d_partial, pr->d_h, st)) return fail(TS_ERR_CUDA, "norm");
+  double h;
+  TS_CUDA(cudaMemcpyAsync(&h, pr->d_h, sizeof(double), cudaMemcpyDeviceToHost, st));
+  TS_CUDA(cudaStreamSynchronize(st));
+  *out = std::sqrt(std::max(h, 0.0));
+  return 0;
+}
+
+int ts_solve(ts_problem* pr, void* y_inout, const ts_solve_opts* opts, ts_solve_report* rep,
+             void* stream) {
+  if (!pr || !y_inout || !opts || !rep) return fail(TS_ERR_ARG, "ts_solve: NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  ts_solve_opts o = *opts;
+  if (o.tol <= 0) o.tol = 1e-8;
+  if (o.max_steps <= 0) o.max_steps = 200;
+  if (o.krylov <= 0) o.krylov = 100;
+  if (o.eps_ls <= 0) o.eps_ls = 0.05;
+  if (o.max_matvec <= 0) o.max_matvec = 10000;
+  if (o.precision != 32 && o.precision != 64) return fail(TS_ERR_ARG, "precision must be 32 or 64");
+  std::memset(rep, 0, sizeof(*rep));
+  TS_TRY(sync_dmask(pr));
+  const int64_t n = field_len(pr);
+  const int m = o.krylov;
+  if (pr->basis_m < m + 1) {
+    dfree(pr->d_basis);
+    TS_TRY(dalloc(&pr->d_basis, (size_t)(m + 1) * n));
+    pr->basis_m = m + 1;
+  }
+  if (!pr->d_w) {
+    TS_TRY(dalloc(&pr->d_w, n));
+    TS_TRY(dalloc(&pr->d_r, n));
+    TS_TRY(dalloc(&pr->d_dy, n));
+    TS_TRY(dalloc(&pr->d_partial, (size_t)krylov_partial_blocks() * 128));
+    TS_TRY(dalloc(&pr->d_h, 128));
+    TS_TRY(dalloc(&pr->d_v32, n));
+    TS_TRY(dalloc(&pr->d_w32, n));
+    TS_TRY(dalloc(&pr->d_D, n));
+    TS_TRY(dalloc(&pr->d_t, n));
+  }
+  if (o.krylov > 128) return fail(TS_ERR_ARG, "ts_solve: krylov must be <= 128");
+  double* y = (double*)y_inout;
+  double* V = pr->d_basis;
+  const double t_start = now_s();
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), yk(m);
+  double r_ref = o.r_ref;
+  int status = TS_ERR_NOCONV;
+  int step = 0;
+  const double dt0 = pr->p.dt_pseudo;
+  const bool ser = o.ser > 0 && dt0 > 0 && std::isfinite(dt0);
+  double r_first = -1;
+  for (step = 0; step <= o.max_steps; ++step) {
+    double t0 = now_s();
+    TS_TRY(ts_residual(pr, y, pr->d_r, 64, st));
+    double rn;
+    TS_TRY(dnorm(pr, pr->d_r, n, st, &rn));
+    rep->t_residual += now_s() - t0;
+    if (!std::isfinite(rn)) {
+      status = fail(TS_ERR_NAN, "ts_solve: non-finite residual norm");
+      break;
+    }
+    if (r_ref <= 0) r_ref = rn;
+    double rel = rn / r_ref;
+    if (rep->hist_len < 512) rep->hist[rep->hist_len++] = rel;
+    rep->r_final = rel;
+    if (o.verbose) fprintf(stderr, "[tsgls] step %d |r|/r_ref = %.3e matvecs %d\n", step, rel, rep->matvecs);
+    if (rel <= o.tol) {
+      status = 0;
+      break;
+    }
+    if (step == o.max_steps) break;
+    if (ser) {
+      if (r_first < 0) r_first = rn;
+      double dt = dt0 * std::pow(r_first / rn, o.ser);
+      pr->p.dt_pseudo = dt > 1e8 * dt0 ? INFINITY : dt;
+    }
+    // right preconditioner: approximate inverse diagonal of the tangent
+    if (o.precond) {
+      TS_CUDA(cudaMemsetAsync(pr->d_D, 0, n * sizeof(double), st));
+      const ts_mesh* msh = pr->mesh;
+      Phys<double> ph = phys_of<double>(pr, true);
+      for (size_t c = 0; c + 1 < msh->colour_off.size(); ++c)
+        if (launch_diag(msh->d_tets, msh->d_geo64, y, pr->p.N, ph, pr->d_D, msh->colour_off[c],
+                        msh->colour_off[c + 1], st))
+          return fail(TS_ERR_CUDA, "diag kernel");
+      if (launch_diag_invert(pr->d_D, pr->d_dmask, msh->V, pr->C, st))
+        return fail(TS_ERR_CUDA, "diag invert");
+    }
+    // GMRES(m) on (H + c1 rho/dt M) D d' = -r, d = D d', from d = 0
+    TS_CUDA(cudaMemsetAsync(pr->d_dy, 0, n * sizeof(double), st));
+    double bnorm = rn;
+    double beta = rn;
+    TS_CUDA(cudaMemcpyAsync(pr->d_w, pr->d_r, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    int nmv = 0;
+    bool done = false;
+    while (!done && nmv < o.max_matvec) {
+      // V0 = -(current linear residual) / beta ; the residual lives in d_w
+      if (vec_scale(V, pr->d_w, -1.0 / beta, n, st)) return fail(TS_ERR_CUDA, "scale");
+      std::fill(g.begin(), g.end(), 0.0);
+      g[0] = beta;
+      int k_used = 0;
+      for (int k = 0; k < m; ++k) {
+        double tj = now_s();
+        double* vk = V + (int64_t)k * n;
+        if (o.precond) {
+          if (vec_mul(pr->d_t, pr->d_D, vk, n, st)) return fail(TS_ERR_CUDA, "mul");
+          vk = pr->d_t;
+        }
+        if (o.precision == 32) {
+          if (vec_cast_d2f(pr->d_v32, vk, n, st)) return fail(TS_ERR_CUDA, "cast");
+          TS_TRY(ts_jvp(pr, pr->d_v32, pr->d_w32, 32, st));
+          if (vec_cast_f2d(pr->d_w, pr->d_w32, n, st)) return fail(TS_ERR_CUDA, "cast");
+        } else {
+          TS_TRY(ts_jvp(pr, vk, pr->d_w, 64, st));
+        }
+        TS_CUDA(cudaStreamSynchronize(st));
+        double tk = now_s();
+        rep->t_jvp += tk - tj;
+        ++nmv;
+        // classical Gram-Schmidt, two passes
+        double hcol[130];
+        for (int j = 0; j <= k + 1; ++j) hcol[j] = 0;
+        for (int pass = 0; pass < 2; ++pass) {
+          if (krylov_dots(V, n, k + 1, pr->d_w, n, pr->d_partial, pr->d_h, st))
+            return fail(TS_ERR_CUDA, "dots");
+          if (krylov_sub(pr->d_w, V, n, k + 1, pr->d_h, n, st)) return fail(TS_ERR_CUDA, "sub");
+          double hh[130];
+          TS_CUDA(cudaMemcpyAsync(hh, pr->d_h, (k + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+          TS_CUDA(cudaStreamSynchronize(st));
+          for (int j = 0; j <= k; ++j) hcol[j] += hh[j];
+        }
+        double hn;
+        TS_TRY(dnorm(pr, pr->d_w, n, st, &hn));
+        hcol[k + 1] = hn;
+        if (hn > 0 && k + 1 < m + 1)
+          if (vec_scale(V + (int64_t)(k + 1) * n, pr->d_w, 1.0 / hn, n, st))
+            return fail(TS_ERR_CUDA, "scale");
+        // Givens rotations on the new Hessenberg column
+        for (int j = 0; j < k; ++j) {
+          double t = cs[j] * hcol[j] + sn[j] * hcol[j + 1];
+          hcol[j + 1] = -sn[j] * hcol[j] + cs[j] * hcol[j + 1];
+          hcol[j] = t;
+        }
+        double d = std::hypot(hcol[k], hcol[k + 1]);
+        cs[k] = d > 0 ? hcol[k] / d : 1.0;
+        sn[k] = d > 0 ? hcol[k + 1] / d : 0.0;
+        hcol[k] = d;
+        for (int j = 0; j <= k; ++j) H[(size_t)j * m + k] = hcol[j];
+        g[k + 1] = -sn[k] * g[k];
+        g[k] = cs[k] * g[k];
+        k_used = k + 1;
+        rep->t_krylov += now_s() - tk;
+        if (std::fabs(g[k + 1]) <= o.eps_ls * bnorm || nmv >= o.max_matvec || hn == 0) break;
+      }
+      // back substitution and update d += V y
+      for (int i = k_used - 1; i >= 0; --i) {
+        double s = g[i];
+        for (int j = i + 1; j < k_used; ++j) s -= H[(size_t)i * m + j] * yk[j];
+        yk[i] = s / H[(size_t)i * m + i];
+      }
+      double tk = now_s();
+      TS_CUDA(cudaMemcpyAsync(pr->d_h, yk.data(), k_used * sizeof(double), cudaMemcpyHostToDevice, st));
+      if (krylov_combine(pr->d_w, V, n, k_used, pr->d_h, n, st)) return fail(TS_ERR_CUDA, "combine");
+      if (o.precond && vec_mul(pr->d_w, pr->d_D, pr->d_w, n, st)) return fail(TS_ERR_CUDA, "mul");
+      if (vec_axpy(pr->d_dy, pr->d_w, 1.0, n, st)) return fail(TS_ERR_CUDA, "axpy");
+      rep->t_krylov += now_s() - tk;
+      double est = std::fabs(g[k_used]);
+      if (est <= o.eps_ls * bnorm || nmv >= o.max_matvec) {
+        done = true;
+      } else {
+        // restart: true linear residual b - J d with b = -r
+        double tj = now_s();
+        if (o.precision == 32) {
+          if (vec_cast_d2f(pr->d_v32, pr->d_dy, n, st)) return fail(TS_ERR_CUDA, "cast");
+          TS_TRY(ts_jvp(pr, pr->d_v32, pr->d_w32, 32, st));
+          if (vec_cast_f2d(pr->d_w, pr->d_w32, n, st)) return fail(TS_ERR_CUDA, "cast");
+        } else {
+          TS_TRY(ts_jvp(pr, pr->d_dy, pr->d_w, 64, st));
+        }
+        ++nmv;
+        rep->t_jvp += now_s() - tj;
+        // d_w = J d + r  (= -(b - J d)), the scale at the loop head negates it
+        if (vec_axpy(pr->d_w, pr->d_r, 1.0, n, st)) return fail(TS_ERR_CUDA, "axpy");
+        TS_TRY(dnorm(pr, pr->d_w, n, st, &beta));
+        if (beta <= o.eps_ls * bnorm) done = true;
+      }
+    }
+    rep->matvecs += nmv;
+    if (vec_axpy(y, pr->d_dy, 1.0, n, st)) return fail(TS_ERR_CUDA, "axpy");
+  }
+  pr->p.dt_pseudo = dt0;
+  TS_CUDA(cudaStreamSynchronize(st));
+  rep->steps = step;
+  rep->r_ref = r_ref;
+  rep->seconds = now_s() - t_start;
+  if (status == TS_ERR_NOCONV) fail(TS_ERR_NOCONV, "ts_solve: step cap reached");
+  return status;
+}
+
+}  // extern "C"

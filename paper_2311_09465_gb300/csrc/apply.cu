@@ -1,0 +1,453 @@
+// Element operator of the time-spectral GLS method: the residual of eq. (Rmc)
+// and the tangent products of eq. (K_mat), section 2.4.
+//
+// Per element and quadrature point q (weights V/4, N_a = barycentric):
+//   c_i   = A_j du_i/dx_j  formed on K = 3N-2 time samples:
+//           modes -> samples (u_j at q, du_i/dx_j), pointwise product,
+//           samples -> modes (exact truncated convolution, eq. phi-def)
+//   L_i   = rho (Omega u_i + c_i) + dp/dx_i       (second derivatives dropped)
+//   T_i   = tau_q L_i                              (tau from the cache, eq. 3D-tau)
+//   r^m_ai += w [N_a rho(Omega u_i + c_i) - N_a Omega T_i] - dN_a/dx_i int p
+//           + mu V dN_a/dx_j du_i/dx_j + dN_a/dx_j sum_q w A_j T_i
+//   r^c_a  += w N_a du_i/dx_i + (w / rho) dN_a/dx_i T_i
+// The SUPG sum sum_q w A_j T_i is formed on samples and transformed once.
+// Modes: RESIDUAL (A, tau at the state itself; also stores T_i per point
+// for the LIN_A product), JVP_PAPER (least-squares parts of G_i and D_j
+// dropped, section 2.5.2: momentum LS sees tau rho(Omega v + A dv), continuity
+// LS sees tau dp), JVP_FROZEN (all of eq. K_mat), JVP_LIN_A (FROZEN plus the
+// derivative of A_j: rho A(v_j) du0_i/dx_j in c_i and dN_a/dx_j A(v_j) T0_i).
+// Pseudo-time adds mass_coef * M v on momentum rows (section 2.5.3).
+//
+// GB300 mapping: one warp per element, all per-element arrays in a per-warp
+// shared-memory workspace, lanes over output entries of each batched small
+// contraction (DFT tables shared per CTA).  Elements of one colour share no
+// node, so each warp adds its 4x4xC results to the nodes without atomics;
+// the host launches the colours in order (deterministic).
+#include "common.cuh"
+#include "kernels.h"
+
+namespace ts {
+
+template <int N, int MODE>
+struct ApplyLayout {
+  using D = Dims<N>;
+  static constexpr int C = D::C, K = D::K, NM = D::NM;
+  static constexpr bool LINA = MODE == MODE_JVP_LIN_A;
+  static constexpr bool PAPER = MODE == MODE_JVP_PAPER;
+  static constexpr int LDF = C | 1;   // odd strides: conflict-free row access
+  static constexpr int LDI = K | 1;
+  static constexpr int TABLES = K * LDF + C * LDI;
+  // per-warp workspace offsets (elements of T)
+  static constexpr int SG = 0;                       // geometry 20 (+4)
+  static constexpr int SV = SG + 24;                 // v at nodes [4][4][C]
+  static constexpr int SU = SV + 16 * C;             // u0 velocity at nodes [4][3][C]
+  static constexpr int GV = SU + 12 * C;             // grad v [4 f][3 j][C]
+  static constexpr int VQ = GV + 12 * C;             // v velocity at points [4][3][C]
+  static constexpr int UQ = VQ + 12 * C;             // u0 velocity at points [4][3][C]
+  static constexpr int PB = UQ + 12 * C;             // mean pressure [C]
+  static constexpr int UQT = PB + C;                 // u0 at points, samples [4][3][K]
+  static constexpr int GVT = UQT + 12 * K;           // grad v samples [3][3][K], later W samples
+  static constexpr int CT = GVT + 9 * K;             // c samples [4][3][K], later T samples
+  static constexpr int CQ = CT + 12 * K;             // rho(Omega v + c) modes [4][3][C]
+  static constexpr int TQ = CQ + 12 * C;             // T modes [4][3][C]
+  static constexpr int TC = TQ + 12 * C;             // PAPER: tau dp [4][3][C]
+  static constexpr int WM = TC + (PAPER ? 12 * C : 0);   // W modes [3][3][C]
+  static constexpr int TAU = WM + 9 * C;             // tau in storage coords [4][NM][NM]
+  static constexpr int OUT = TAU + 4 * NM * NM;      // [4][4][C]
+  static constexpr int GU = OUT + 16 * C;            // LIN_A: grad u0 [3][3][C]
+  static constexpr int VQT = GU + (LINA ? 9 * C : 0);    // LIN_A: v at points samples
+  static constexpr int GUT = VQT + (LINA ? 12 * K : 0);  // LIN_A: grad u0 samples
+  static constexpr int T0 = GUT + (LINA ? 9 * K : 0);    // LIN_A: T0 modes
+  static constexpr int T0T = T0 + (LINA ? 12 * C : 0);   // LIN_A: T0 samples
+  static constexpr int END = T0T + (LINA ? 12 * K : 0);
+  static constexpr int WARP = (END + 3) & ~3;
+};
+
+// out[b*os + r] = sum_c M[r*ld + c] in[b*is + c]
+template <typename T, int R, int CN>
+__device__ __forceinline__ void warp_bmv(const T* __restrict__ M, int ld, const T* in, int is,
+                                         T* out, int os, int B, int lane) {
+  for (int t = lane; t < B * R; t += 32) {
+    const int b = t / R, r = t - (t / R) * R;
+    const T* mr = M + r * ld;
+    const T* x = in + b * is;
+    T acc = 0;
+#pragma unroll
+    for (int c = 0; c < CN; ++c) acc = fma(mr[c], x[c], acc);
+    out[b * os + r] = acc;
+  }
+}
+
+// (Omega x) in storage coordinates: mode n -> i n omega x_n
+template <typename T>
+__device__ __forceinline__ T omega_apply(const T* x, int c, T omega) {
+  const int n = c >> 1;
+  return (c & 1) ? T(n) * omega * x[c - 1] : -T(n) * omega * x[c + 1];
+}
+
+template <typename T, int N, int MODE>
+__global__ void __launch_bounds__(128)
+    apply_kernel(const int4* __restrict__ tets, const T* __restrict__ geo,
+                 const T* __restrict__ v, const T* __restrict__ u0, const T* __restrict__ tau,
+                 T* __restrict__ t0cache, const uint8_t* __restrict__ dmask, T* __restrict__ out,
+                 const T* __restrict__ dft, Phys<T> ph, int64_t e0, int64_t e1) {
+  using D = Dims<N>;
+  using L = ApplyLayout<N, MODE>;
+  constexpr int C = D::C, K = D::K, NM = D::NM, NT = D::NT, NTP = D::NT_PAD;
+  constexpr bool RES = MODE == MODE_RESIDUAL;
+  constexpr bool PAPER = MODE == MODE_JVP_PAPER;
+  constexpr bool LINA = MODE == MODE_JVP_LIN_A;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sF = reinterpret_cast<T*>(smem_raw);   // forward DFT [K][LDF]
+  T* sI = sF + K * L::LDF;                  // inverse DFT [C][LDI]
+  for (int t = threadIdx.x; t < K * C; t += blockDim.x) {
+    const int kk = t / C, c = t - kk * C;
+    sF[kk * L::LDF + c] = dft[t];
+  }
+  for (int t = threadIdx.x; t < C * K; t += blockDim.x) {
+    const int c = t / K, kk = t - c * K;
+    sI[c * L::LDI + kk] = dft[K * C + t];
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T* ws = sF + L::TABLES + warp * L::WARP;
+  T* sg = ws + L::SG;
+  T* sv = ws + L::SV;
+  T* su = ws + L::SU;
+  T* gv = ws + L::GV;
+  T* vq = ws + L::VQ;
+  T* uq = ws + L::UQ;
+  T* pb = ws + L::PB;
+  T* uqt = ws + L::UQT;
+  T* gvt = ws + L::GVT;
+  T* ct = ws + L::CT;
+  T* cq = ws + L::CQ;
+  T* tq = ws + L::TQ;
+  T* tc = PAPER ? ws + L::TC : tq;
+  T* wm = ws + L::WM;
+  T* st = ws + L::TAU;
+  T* so = ws + L::OUT;
+  T* gu = ws + L::GU;
+  T* vqt = ws + L::VQT;
+  T* gut = ws + L::GUT;
+  T* t0 = ws + L::T0;
+  T* t0t = ws + L::T0T;
+  const T rho = ph.rho, omega = ph.omega;
+  const int wpb = blockDim.x >> 5;
+
+  for (int64_t e = e0 + (int64_t)blockIdx.x * wpb + warp; e < e1;
+       e += (int64_t)gridDim.x * wpb) {
+    const int4 nd = tets[e];
+    const int node[4] = {nd.x, nd.y, nd.z, nd.w};
+    if (lane < GEO_STRIDE) sg[lane] = geo[e * GEO_STRIDE + lane];
+    for (int t = lane; t < 16 * C; t += 32) {
+      const int a = t / (4 * C), r = t - a * 4 * C;
+      const int f = r / C, c = r - f * C;
+      T val = v[(int64_t)node[a] * 4 * C + r];
+      if (c == 1) val = T(0);
+      if (!RES && f < 3 && dmask[node[a]]) val = T(0);
+      sv[t] = val;
+    }
+    for (int t = lane; t < 12 * C; t += 32) {
+      const int a = t / (3 * C), r = t - a * 3 * C;
+      const int c = r % C;
+      T val = u0[(int64_t)node[a] * 4 * C + r];
+      su[t] = (c == 1) ? T(0) : val;
+    }
+    // tau: packed symmetric (orthonormal basis) -> full matrix in storage scaling
+    {
+      const T* tp = tau + e * 4 * NTP;
+      for (int t = lane; t < 4 * NTP; t += 32) {
+        const int q = t / NTP, p = t - q * NTP;
+        if (p >= NT) continue;
+        int r = 0, rem = p;
+        while (rem >= NM - r) {
+          rem -= NM - r;
+          ++r;
+        }
+        const int s = r + rem;
+        const T val = tp[t];
+        // T_s[r] = (1/d_r) sum_k tau[r][k] d_k L_s[k], d_0 = 1, d_k = sqrt2
+        const T drs = (r == 0 && s > 0) ? Real<T>::SQRT2 : T(1);
+        const T dsr = (r == 0 && s > 0) ? Real<T>::INV_SQRT2 : T(1);
+        st[q * NM * NM + r * NM + s] = val * drs;
+        st[q * NM * NM + s * NM + r] = val * dsr;
+      }
+    }
+    if (LINA) {
+      const T* tp = t0cache + e * 12 * C;
+      for (int t = lane; t < 12 * C; t += 32) t0[t] = tp[t];
+    }
+    __syncwarp();
+    const T vol = sg[GEO_VOL];
+    // ---- phase 1: gradients, point values (modes)
+    for (int t = lane; t < 12 * C; t += 32) {
+      const int f = t / (3 * C), r = t - f * 3 * C;
+      const int j = r / C, c = r - j * C;
+      T acc = 0;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) acc += sg[a * 3 + j] * sv[a * 4 * C + f * C + c];
+      gv[t] = acc;
+    }
+    for (int t = lane; t < 12 * C; t += 32) {
+      const int q = t / (3 * C), r = t - q * 3 * C;   // r = i*C + c
+      T av = 0, au = 0;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const T lam = (T)qp_bary(q, a);
+        av += lam * sv[a * 4 * C + r];
+        au += lam * su[a * 3 * C + r];
+      }
+      vq[t] = av;
+      uq[t] = au;
+    }
+    for (int c = lane; c < C; c += 32)
+      pb[c] = T(0.25) * (sv[3 * C + c] + sv[7 * C + c] + sv[11 * C + c] + sv[15 * C + c]);
+    if (LINA) {
+      for (int t = lane; t < 9 * C; t += 32) {
+        const int i = t / (3 * C), r = t - i * 3 * C;
+        const int j = r / C, c = r - j * C;
+        T acc = 0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) acc += sg[a * 3 + j] * su[a * 3 * C + i * C + c];
+        gu[t] = acc;   // du0_i/dx_j at [i][j][c]
+      }
+    }
+    __syncwarp();
+    // ---- phase 2: modes -> samples
+    warp_bmv<T, K, C>(sF, L::LDF, uq, C, uqt, K, 12, lane);
+    warp_bmv<T, K, C>(sF, L::LDF, gv, C, gvt, K, 9, lane);   // velocity gradients only
+    if (LINA) {
+      warp_bmv<T, K, C>(sF, L::LDF, vq, C, vqt, K, 12, lane);
+      warp_bmv<T, K, C>(sF, L::LDF, gu, C, gut, K, 9, lane);
+    }
+    __syncwarp();
+    // ---- phase 3: convective products on samples: c_i = u0_j dv_i/dx_j (+ v_j du0_i/dx_j)
+    for (int t = lane; t < 12 * K; t += 32) {
+      const int q = t / (3 * K), r = t - q * 3 * K;
+      const int i = r / K, kk = r - i * K;
+      T acc = 0;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) acc += uqt[(q * 3 + j) * K + kk] * gvt[(i * 3 + j) * K + kk];
+      if (LINA) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) acc += vqt[(q * 3 + j) * K + kk] * gut[(i * 3 + j) * K + kk];
+      }
+      ct[t] = acc;
+    }
+    __syncwarp();
+    // ---- phase 4: samples -> modes (truncation to |m| < N)
+    warp_bmv<T, C, K>(sI, L::LDI, ct, K, cq, C, 12, lane);
+    __syncwarp();
+    // ---- phase 5: rho (Omega v + c) at each point (in place)
+    for (int t = lane; t < 12 * C; t += 32) {
+      const int c = t % C;
+      const T om = (c == 1) ? T(0) : omega_apply(vq + (t - c), c, omega);
+      cq[t] = (c == 1) ? T(0) : rho * (om + cq[t]);
+    }
+    __syncwarp();
+    // ---- phase 6: T = tau L (storage coordinates)
+    for (int t = lane; t < 12 * NM; t += 32) {
+      const int qi = t / NM, r = t - qi * NM;
+      const int q = qi / 3, i = qi - q * 3;
+      const T* tr = st + q * NM * NM + r * NM;
+      const T* lu = cq + qi * C;
+      const T* lp = gv + (9 + i) * C;     // dp/dx_i
+      T acc = 0, accp = 0;
+#pragma unroll
+      for (int kk = 0; kk < NM; ++kk) {
+        const int cs = stor_of(kk);
+        if (PAPER) {
+          acc += tr[kk] * lu[cs];
+          accp += tr[kk] * lp[cs];
+        } else {
+          acc += tr[kk] * (lu[cs] + lp[cs]);
+        }
+      }
+      tq[qi * C + stor_of(r)] = acc;
+      if (PAPER) tc[qi * C + stor_of(r)] = accp;
+    }
+    for (int qi = lane; qi < 12; qi += 32) {
+      tq[qi * C + 1] = T(0);
+      if (PAPER) tc[qi * C + 1] = T(0);
+    }
+    __syncwarp();
+    if (RES) {
+      T* tp = t0cache + e * 12 * C;
+      for (int t = lane; t < 12 * C; t += 32) tp[t] = tq[t];
+    }
+    // ---- phase 7: T (and T0) to samples
+    warp_bmv<T, K, C>(sF, L::LDF, tq, C, ct, K, 12, lane);
+    if (LINA) warp_bmv<T, K, C>(sF, L::LDF, t0, C, t0t, K, 12, lane);
+    __syncwarp();
+    // ---- phase 8: SUPG sums on samples W_ji = sum_q u0_j T_i (+ v_j T0_i)
+    for (int t = lane; t < 9 * K; t += 32) {
+      const int ji = t / K, kk = t - ji * K;
+      const int j = ji / 3, i = ji - j * 3;
+      T acc = 0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc += uqt[(q * 3 + j) * K + kk] * ct[(q * 3 + i) * K + kk];
+      if (LINA) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc += vqt[(q * 3 + j) * K + kk] * t0t[(q * 3 + i) * K + kk];
+      }
+      gvt[t] = acc;
+    }
+    __syncwarp();
+    // ---- phase 9: W to modes
+    warp_bmv<T, C, K>(sI, L::LDI, gvt, K, wm, C, 9, lane);
+    __syncwarp();
+    // ---- phase 10: element contributions per node
+    const T w4 = T(0.25) * vol;
+    for (int t = lane; t < 16 * C; t += 32) {
+      const int a = t / (4 * C), r = t - a * 4 * C;
+      const int f = r / C, c = r - f * C;
+      T acc = 0;
+      if (c != 1) {
+        if (f < 3) {
+          const int i = f;
+          T gal = 0;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const T lam = (T)qp_bary(q, a);
+            const T* tqi = tq + (q * 3 + i) * C;
+            gal += lam * (cq[(q * 3 + i) * C + c] - omega_apply(tqi, c, omega));
+          }
+          acc = w4 * gal - sg[a * 3 + i] * vol * pb[c];
+          T visc = 0, supg = 0;
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            visc += sg[a * 3 + j] * gv[(i * 3 + j) * C + c];
+            supg += sg[a * 3 + j] * wm[(j * 3 + i) * C + c];
+          }
+          acc += ph.mu * vol * visc + w4 * supg;
+          if (!RES && ph.mass_coef != T(0)) {
+            T sum = sv[a * 4 * C + i * C + c];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) sum += sv[b * 4 * C + i * C + c];
+            acc += ph.mass_coef * vol * T(0.05) * sum;
+          }
+        } else {
+          const T div = gv[(0 * 3 + 0) * C + c] + gv[(1 * 3 + 1) * C + c] + gv[(2 * 3 + 2) * C + c];
+          T ls = 0;
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) ls += sg[a * 3 + i] * tc[(q * 3 + i) * C + c];
+          acc = w4 * div + (w4 / rho) * ls;
+        }
+      }
+      so[t] = acc;
+    }
+    __syncwarp();
+    // ---- phase 11: colour-exclusive scatter-add
+    for (int t = lane; t < 16 * C; t += 32) {
+      const int a = t / (4 * C), r = t - a * 4 * C;
+      const int f = r / C, c = r - f * C;
+      if (c == 1) continue;
+      if (f < 3 && dmask[node[a]]) continue;
+      T* dst = out + (int64_t)node[a] * 4 * C + r;
+      *dst += so[t];
+    }
+    __syncwarp();
+  }
+}
+
+template <typename T, int N, int MODE>
+static int launch_mode(const int4* tets, const T* geo, const T* v, const T* u0, const T* tau,
+                       T* t0cache, const uint8_t* dmask, T* out, const T* dft, Phys<T> ph,
+                       int64_t e0, int64_t e1, cudaStream_t st) {
+  using L = ApplyLayout<N, MODE>;
+  if (e1 <= e0) return 0;
+  int warps = 4;
+  while (warps > 1 && (size_t)(L::TABLES + warps * L::WARP) * sizeof(T) > 200 * 1024) --warps;
+  const size_t smem = (size_t)(L::TABLES + warps * L::WARP) * sizeof(T);
+  if (smem > 227 * 1024) return -6;
+  cudaFuncSetAttribute(apply_kernel<T, N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)smem);
+  int64_t blocks = (e1 - e0 + warps - 1) / warps;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  count_launches(1);
+  apply_kernel<T, N, MODE><<<(int)blocks, warps * 32, smem, st>>>(tets, geo, v, u0, tau, t0cache,
+                                                                  dmask, out, dft, ph, e0, e1);
+  return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+template <typename T, int N>
+int launch_apply(int mode, const int4* tets, const T* geo, const T* v, const T* u0,
+                 const T* tau, T* t0cache, const uint8_t* dmask, T* out, const T* dft,
+                 Phys<T> ph, int64_t e0, int64_t e1, cudaStream_t st) {
+  switch (mode) {
+    case MODE_RESIDUAL:
+      return launch_mode<T, N, MODE_RESIDUAL>(tets, geo, v, u0, tau, t0cache, dmask, out, dft,
+                                              ph, e0, e1, st);
+    case MODE_JVP_PAPER:
+      return launch_mode<T, N, MODE_JVP_PAPER>(tets, geo, v, u0, tau, t0cache, dmask, out, dft,
+                                               ph, e0, e1, st);
+    case MODE_JVP_FROZEN:
+      return launch_mode<T, N, MODE_JVP_FROZEN>(tets, geo, v, u0, tau, t0cache, dmask, out, dft,
+                                                ph, e0, e1, st);
+    case MODE_JVP_LIN_A:
+      return launch_mode<T, N, MODE_JVP_LIN_A>(tets, geo, v, u0, tau, t0cache, dmask, out, dft,
+                                               ph, e0, e1, st);
+  }
+  return -1;
+}
+
+// ---------------------------------------------------------------- outlets
+// One block per call: Q_c = sum_A sum_i w_Ai v[A][i][c]; out[A][i][c] += R w_Ai Q_c
+template <typename T>
+__global__ void outlet_kernel(const int32_t* __restrict__ nodes, const T* __restrict__ w, int n,
+                              T R, const T* __restrict__ v, const uint8_t* __restrict__ dmask,
+                              int mask_input, T* __restrict__ out, int C) {
+  __shared__ T part[256];
+  __shared__ T Q[128];
+  for (int c = 0; c < C; ++c) {
+    T acc = 0;
+    for (int b = threadIdx.x; b < n; b += blockDim.x) {
+      const int A = nodes[b];
+      if (mask_input && dmask[A]) continue;
+      const T* va = v + (int64_t)A * 4 * C;
+      acc += w[b * 3 + 0] * va[0 * C + c] + w[b * 3 + 1] * va[1 * C + c] + w[b * 3 + 2] * va[2 * C + c];
+    }
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s) part[threadIdx.x] += part[threadIdx.x + s];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) Q[c] = (c == 1) ? T(0) : part[0];
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < n * 3 * C; t += blockDim.x) {
+    const int b = t / (3 * C), r = t - b * 3 * C;
+    const int i = r / C, c = r - i * C;
+    const int A = nodes[b];
+    if (dmask[A] || c == 1) continue;
+    out[(int64_t)A * 4 * C + i * C + c] += R * w[b * 3 + i] * Q[c];
+  }
+}
+
+template <typename T>
+int launch_outlet(const int32_t* nodes, const T* w, int n_nodes, T R, const T* v,
+                  const uint8_t* dmask, int mask_input, T* out, int C, cudaStream_t st) {
+  if (n_nodes <= 0) return 0;
+  if (C > 128) return -1;
+  count_launches(1);
+  outlet_kernel<T><<<1, 256, 0, st>>>(nodes, w, n_nodes, R, v, dmask, mask_input, out, C);
+  return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+template int launch_outlet<float>(const int32_t*, const float*, int, float, const float*,
+                                  const uint8_t*, int, float*, int, cudaStream_t);
+template int launch_outlet<double>(const int32_t*, const double*, int, double, const double*,
+                                   const uint8_t*, int, double*, int, cudaStream_t);
+
+#define TS_INST_APPLY(T, N)                                                                  \
+  template int launch_apply<T, N>(int, const int4*, const T*, const T*, const T*, const T*, \
+                                  T*, const uint8_t*, T*, const T*, Phys<T>, int64_t,        \
+                                  int64_t, cudaStream_t);
+TS_FOR_EACH_N(TS_INST_APPLY, float)
+TS_FOR_EACH_N(TS_INST_APPLY, double)
+
+}  // namespace ts

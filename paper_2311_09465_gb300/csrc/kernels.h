@@ -1,0 +1,71 @@
+// Kernel launchers of the GB300 time-spectral GLS library (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+// Mode counts with compiled kernels.  Each entry instantiates the tau,
+// operator and boundary kernels in FP32 and FP64.
+#define TS_FOR_EACH_N(X, T) X(T, 1) X(T, 2) X(T, 3) X(T, 4) X(T, 5) X(T, 7) X(T, 10) X(T, 15)
+#define TS_N_LIST 1, 2, 3, 4, 5, 7, 10, 15
+
+namespace ts {
+
+// process-wide count of kernel launches issued by this library
+void count_launches(int n);
+unsigned long long launches_total();
+
+template <typename T, int N>
+int launch_tau(const int4* tets, const T* geo, const T* y, int64_t n_elem, T* tau_out, T nu,
+               T C_I, unsigned* n_unconverged, cudaStream_t st);
+
+// One colour range [e0, e1) of the element operator (see apply.cu).
+template <typename T, int N>
+int launch_apply(int mode, const int4* tets, const T* geo, const T* v, const T* u0,
+                 const T* tau, T* t0cache, const uint8_t* dmask, T* out, const T* dft,
+                 Phys<T> ph, int64_t e0, int64_t e1, cudaStream_t st);
+
+// Resistance outlets: out[A][i][c] += R w_Ai Q_c with Q_c = sum_B w_Bi v[B][i][c]
+template <typename T>
+int launch_outlet(const int32_t* nodes, const T* w, int n_nodes, T R, const T* v,
+                  const uint8_t* dmask, int mask_input, T* out, int C, cudaStream_t st);
+
+// FP32 tangent product, one launch (jvp32.cu); out must be zero on entry
+template <int N>
+int launch_jvp32(int mode, const int4* tets, const float* geo, const float* v, const float* u0t,
+                 const float* tau, const float* t0, const uint8_t* dmask, float* out,
+                 Phys<float> ph, int64_t n_elem, cudaStream_t st);
+// u0 velocity at the nodes as time samples [V][3][K]
+template <int N>
+int launch_node_samples(const float* u0, float* u0t, int64_t V, cudaStream_t st);
+// the table of all compiled N (forward [K][C] then inverse [C][K] each)
+int dft_constant_total();
+int dft_constant_offset(int N);
+// each fast-path translation unit copies its slice into its constant bank
+int j32_upload_n123(const float* host_all);
+int j32_upload_n45(const float* host_all);
+int j32_upload_n7(const float* host_all);
+constexpr int J32_MAX_N = 7;   // largest N with the single-launch FP32 kernel
+
+// FP64 Krylov helpers (krylov.cu)
+int krylov_dots(const double* basis, int64_t ld, int nvec, const double* w, int64_t n,
+                double* partial, double* h_out, cudaStream_t st);
+int krylov_sub(double* w, const double* basis, int64_t ld, int nvec, const double* h, int64_t n,
+               cudaStream_t st);
+int krylov_combine(double* x, const double* basis, int64_t ld, int nvec, const double* coef,
+                   int64_t n, cudaStream_t st);
+int vec_scale(double* out, const double* in, double a, int64_t n, cudaStream_t st);
+int vec_axpy(double* y, const double* x, double a, int64_t n, cudaStream_t st);
+int vec_cast_d2f(float* out, const double* in, int64_t n, cudaStream_t st);
+int vec_cast_f2d(double* out, const float* in, int64_t n, cudaStream_t st);
+int krylov_partial_blocks();
+int vec_mul(double* out, const double* a, const double* b, int64_t n, cudaStream_t st);
+// approximate diagonal of the tangent for right preconditioning (one colour range)
+int launch_diag(const int4* tets, const double* geo, const double* y, int N, Phys<double> ph,
+                double* D, int64_t e0, int64_t e1, cudaStream_t st);
+// D <- 1/D on free unknowns, 1 on fixed ones
+int launch_diag_invert(double* D, const uint8_t* dmask, int64_t V, int C, cudaStream_t st);
+
+}  // namespace ts

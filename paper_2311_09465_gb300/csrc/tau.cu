@@ -1,0 +1,278 @@
+// tau at every quadrature point, eq. (3D-tau):
+//   tau = [A_i G_ij A_j + C_I nu^2 G_ij G_ij I]^{-1/2}
+// computed, as the paper prescribes after eq. (3D-tau), from the eigenpairs
+// of the matrix under the root (section 2.2), at every quadrature point
+// (section 4).
+//
+// GB300 mapping: a group of N lanes owns one quadrature point; a warp holds
+// floor(32/N) points.  With G = L L^T (3x3 Cholesky) the argument becomes
+// M = sum_m C_m C_m + C_I nu^2 (G:G) I, C_m = A(w_m), w_m = sum_i L_im u_i,
+// because the convolution matrix is linear in the velocity modes.  The
+// symmetric eigenproblem of the real (2N-1)x(2N-1) form of M is solved by
+// parallel cyclic Jacobi (round-robin ordering, N disjoint rotations per
+// round, one per lane), padded with a decoupled dummy row to size 2N.
+// tau = V diag(lambda^{-1/2}) V^T is written as a packed upper triangle.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace ts {
+
+// entry (r, s) of the real symmetric convolution matrix of a (storage
+// coordinates a[0..C-1]) in the orthonormal basis (x0, sqrt2 Re, sqrt2 Im)
+template <typename T, int N>
+__device__ __forceinline__ T conv_entry(const T* a, int r, int s) {
+  auto ar = [&](int k) -> T {
+    int m = k < 0 ? -k : k;
+    return m < N ? a[2 * m] : T(0);
+  };
+  auto ai = [&](int k) -> T {
+    int m = k < 0 ? -k : k;
+    if (m >= N || m == 0) return T(0);
+    return k > 0 ? a[2 * m + 1] : -a[2 * m + 1];
+  };
+  if (r == 0 && s == 0) return a[0];
+  const T s2 = Real<T>::SQRT2;
+  if (r == 0 || s == 0) {
+    int o = r == 0 ? s : r;
+    int n = (o + 1) >> 1;
+    return (o & 1) ? s2 * ar(n) : s2 * ai(n);
+  }
+  int m = (r + 1) >> 1, n = (s + 1) >> 1;
+  bool rre = r & 1, sre = s & 1;
+  if (rre && sre) return ar(m - n) + ar(m + n);
+  if (rre && !sre) return ai(m + n) - ai(m - n);
+  if (!rre && sre) return ai(m - n) + ai(m + n);
+  return ar(m - n) - ar(m + n);
+}
+
+template <int N>
+struct TauLayout {
+  using D = Dims<N>;
+  static constexpr int NP = D::NP, NM = D::NM, C = D::C;
+  static constexpr int LD = NP + 1;
+  static constexpr int GPW = 32 / N;
+  static constexpr int CM = 0;                       // [3][NM][NM]
+  static constexpr int M = CM + 3 * NM * NM;         // [NP][LD]
+  static constexpr int V = M + NP * LD;              // [NP][LD]
+  static constexpr int W = V + NP * LD;              // [3][C]
+  static constexpr int GROUP = ((W + 3 * C) + 1) & ~1;
+  static constexpr int WARP = GPW * GROUP + 64;      // + reduction scratch
+};
+
+template <typename T, int N>
+__global__ void __launch_bounds__(128) tau_kernel(const int4* __restrict__ tets,
+                                                  const T* __restrict__ geo,
+                                                  const T* __restrict__ y, int64_t n_qp,
+                                                  T* __restrict__ tau_out, T nu, T C_I,
+                                                  int max_sweeps, T tol2,
+                                                  unsigned* __restrict__ n_unconverged) {
+  using D = Dims<N>;
+  using L = TauLayout<N>;
+  constexpr int NP = D::NP, NM = D::NM, C = D::C, LD = L::LD, GPW = L::GPW;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* smem = reinterpret_cast<T*>(smem_raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane / N, k = lane - (lane / N) * N;
+  const bool in_group = g < GPW;
+  T* wbase = smem + warp * L::WARP;
+  T* base = wbase + (in_group ? g : 0) * L::GROUP;
+  T* Cm = base + L::CM;
+  T* M = base + L::M;
+  T* Vv = base + L::V;
+  T* w = base + L::W;
+  T* red = wbase + GPW * L::GROUP;       // [32] partial sums, [32..] flags
+
+  const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t qb = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * GPW; qb < n_qp;
+       qb += warps_total * GPW) {
+    const int64_t gq = qb + g;
+    const bool live = in_group && gq < n_qp;
+    const int64_t e = live ? gq >> 2 : 0;
+    const int q = (int)(gq & 3);
+    T l00 = 0, l10 = 0, l20 = 0, l11 = 0, l21 = 0, l22 = 0, diff = 0;
+    if (live) {
+      const T* gg = geo + e * GEO_STRIDE + GEO_G;
+      T gxx = gg[0], gxy = gg[1], gxz = gg[2], gyy = gg[3], gyz = gg[4], gzz = gg[5];
+      l00 = Real<T>::sqrt(gxx);
+      l10 = gxy / l00;
+      l20 = gxz / l00;
+      l11 = Real<T>::sqrt(gyy - l10 * l10);
+      l21 = (gyz - l20 * l10) / l11;
+      l22 = Real<T>::sqrt(gzz - l20 * l20 - l21 * l21);
+      T GG = gxx * gxx + gyy * gyy + gzz * gzz + T(2) * (gxy * gxy + gxz * gxz + gyz * gyz);
+      diff = C_I * nu * nu * GG;
+      const int4 nd = tets[e];
+      const int node[4] = {nd.x, nd.y, nd.z, nd.w};
+      // velocity modes at the point, then w_m = sum_i L_im u_i
+      for (int c = k; c < C; c += N) {
+        T u[3] = {0, 0, 0};
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const T lam = (T)qp_bary(q, a);
+          const T* ya = y + (int64_t)node[a] * 4 * C;
+#pragma unroll
+          for (int i = 0; i < 3; ++i) u[i] += lam * ya[i * C + c];
+        }
+        if (c == 1) u[0] = u[1] = u[2] = 0;
+        w[0 * C + c] = l00 * u[0] + l10 * u[1] + l20 * u[2];
+        w[1 * C + c] = l11 * u[1] + l21 * u[2];
+        w[2 * C + c] = l22 * u[2];
+      }
+    }
+    __syncwarp();
+    if (live) {
+      for (int t = k; t < 3 * NM * NM; t += N) {
+        int m = t / (NM * NM), rs = t - m * NM * NM;
+        int r = rs / NM, s = rs - r * NM;
+        Cm[t] = conv_entry<T, N>(w + m * C, r, s);
+      }
+    }
+    __syncwarp();
+    if (live) {
+      for (int t = k; t < NP * NP; t += N) {
+        int r = t / NP, s = t - r * NP;
+        if (r > s) continue;
+        T acc = 0;
+        if (r < NM && s < NM) {
+#pragma unroll
+          for (int m = 0; m < 3; ++m) {
+            const T* cr = Cm + m * NM * NM + r * NM;
+            const T* cs = Cm + m * NM * NM + s * NM;
+            for (int j = 0; j < NM; ++j) acc += cr[j] * cs[j];
+          }
+          if (r == s) acc += diff;
+        } else if (r == s) {
+          acc = T(1);                      // decoupled dummy
+        }
+        M[r * LD + s] = acc;
+        M[s * LD + r] = acc;
+        Vv[r * LD + s] = (r == s) ? T(1) : T(0);
+        Vv[s * LD + r] = (r == s) ? T(1) : T(0);
+      }
+    }
+    __syncwarp();
+    // parallel cyclic Jacobi
+    constexpr int P = NP - 1;
+    bool converged = false;
+    int sweep = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+      for (int rr = 0; rr < P; ++rr) {
+        int p, qq;
+        if (k == 0) {
+          p = 0;
+          qq = 1 + rr % P;
+        } else {
+          p = 1 + (rr + k) % P;
+          qq = 1 + (rr - k + P) % P;
+        }
+        T c = 1, s = 0;
+        if (live) {
+          T app = M[p * LD + p], aqq = M[qq * LD + qq], apq = M[p * LD + qq];
+          if (apq != T(0)) {
+            T zeta = (aqq - app) / (T(2) * apq);
+            T t = T(1) / (fabs(zeta) + Real<T>::sqrt(T(1) + zeta * zeta));
+            if (zeta < T(0)) t = -t;
+            c = Real<T>::rsqrt(T(1) + t * t);
+            s = t * c;
+          }
+        }
+        __syncwarp();
+        if (live && s != T(0)) {
+          for (int j = 0; j < NP; ++j) {
+            T mp = M[p * LD + j], mq = M[qq * LD + j];
+            M[p * LD + j] = c * mp - s * mq;
+            M[qq * LD + j] = s * mp + c * mq;
+          }
+        }
+        __syncwarp();
+        if (live && s != T(0)) {
+          for (int i = 0; i < NP; ++i) {
+            T mp = M[i * LD + p], mq = M[i * LD + qq];
+            M[i * LD + p] = c * mp - s * mq;
+            M[i * LD + qq] = s * mp + c * mq;
+            T vp = Vv[i * LD + p], vq = Vv[i * LD + qq];
+            Vv[i * LD + p] = c * vp - s * vq;
+            Vv[i * LD + qq] = s * vp + c * vq;
+          }
+          M[p * LD + qq] = T(0);
+          M[qq * LD + p] = T(0);
+        }
+        __syncwarp();
+      }
+      // convergence: sum of squared off-diagonals vs squared diagonal
+      T off = 0, dg = 0;
+      if (live) {
+        for (int r = k; r < NM; r += N) {
+          dg += M[r * LD + r] * M[r * LD + r];
+          for (int s = r + 1; s < NM; ++s) off += M[r * LD + s] * M[r * LD + s];
+        }
+      }
+      red[lane] = off;
+      red[32 + lane] = dg;
+      __syncwarp();
+      bool mine = true;
+      if (live) {
+        T so = 0, sd = 0;
+        for (int j = 0; j < N; ++j) {
+          so += red[g * N + j];
+          sd += red[32 + g * N + j];
+        }
+        mine = so <= tol2 * sd;
+      }
+      __syncwarp();
+      converged = mine;
+      if (__all_sync(0xffffffffu, !live || mine)) break;
+    }
+    if (live && k == 0 && !converged) atomicAdd(n_unconverged, 1u);
+    // tau = V diag(lambda^{-1/2}) V^T, packed upper triangle
+    if (live) {
+      T* out = tau_out + gq * Dims<N>::NT_PAD;
+      for (int t = k; t < NM * NM; t += N) {
+        int r = t / NM, s = t - r * NM;
+        if (r > s) continue;
+        T acc = 0;
+        for (int j = 0; j < NM; ++j) {
+          T lam = M[j * LD + j];
+          acc += Vv[r * LD + j] * Vv[s * LD + j] * Real<T>::rsqrt(lam);
+        }
+        out[packed_index(r, s, NM)] = acc;
+      }
+      if (k == 0)
+        for (int t = Dims<N>::NT; t < Dims<N>::NT_PAD; ++t) out[t] = T(0);
+    }
+    __syncwarp();
+  }
+}
+
+template <typename T, int N>
+int launch_tau(const int4* tets, const T* geo, const T* y, int64_t n_elem, T* tau_out, T nu,
+               T C_I, unsigned* n_unconverged, cudaStream_t st) {
+  using L = TauLayout<N>;
+  const int warps = 4;
+  size_t smem = (size_t)warps * L::WARP * sizeof(T);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(tau_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    attr_set = true;
+  }
+  int64_t n_qp = n_elem * 4;
+  int64_t groups = (n_qp + L::GPW - 1) / L::GPW;
+  int64_t blocks = (groups + warps - 1) / warps;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  if (blocks < 1) blocks = 1;
+  const int sweeps = sizeof(T) == 4 ? 12 : 20;
+  const T tol2 = sizeof(T) == 4 ? T(1e-12) : T(1e-28);
+  count_launches(1);
+  tau_kernel<T, N><<<(int)blocks, warps * 32, smem, st>>>(tets, geo, y, n_qp, tau_out, nu, C_I,
+                                                          sweeps, tol2, n_unconverged);
+  return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+#define TS_INST_TAU(T, N)                                                                 \
+  template int launch_tau<T, N>(const int4*, const T*, const T*, int64_t, T*, T, T,       \
+                                unsigned*, cudaStream_t);
+TS_FOR_EACH_N(TS_INST_TAU, float)
+TS_FOR_EACH_N(TS_INST_TAU, double)
+
+}  // namespace ts
