@@ -85,6 +85,8 @@ typedef struct {
   double ser;          /* > 0: pseudo-time step grows as dt_k = dt_0 (|r_0|/|r_k|)^ser
                           (switched evolution relaxation; dt_0 = the problem's
                           dt_pseudo, which must be finite); 0: fixed dt (section 2.5.3) */
+  double dt_max;       /* > 0: upper bound of the grown pseudo-time step (keeps the mass
+                          term in the tangent, so GMRES stays effective); 0: no bound */
 } ts_solve_opts;
 
 typedef struct {

@@ -117,6 +117,7 @@ struct ts_problem {
   float *d_v32 = nullptr, *d_w32 = nullptr;
   double *d_D = nullptr, *d_t = nullptr;      // preconditioner diagonal (inverted), temp
   bool fast32 = true;    // FP32 products with the single-launch kernel (jvp32.cu)
+  bool tau_exact64 = false;  // FP64 tau by FP64 Jacobi instead of FP32 Jacobi + FP64 polish
 };
 
 // ------------------------------------------------------------------ helpers
@@ -268,8 +269,18 @@ static int residual_impl(ts_problem* pr, const T* y, T* r, cudaStream_t st) {
   TS_TRY(lin_alloc(pr, l));
   const int64_t n = field_len(pr);
   TS_CUDA(cudaMemcpyAsync(l.u0, y, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
-  int rc = launch_tau<T, N>(m->d_tets, geo_of<T>(m), y, m->E, l.tau, (T)(pr->p.mu / pr->p.rho),
+  int rc;
+  if constexpr (sizeof(T) == 8) {
+    if (pr->tau_exact64)
+      rc = launch_tau<T, N>(m->d_tets, geo_of<T>(m), y, m->E, l.tau, (T)(pr->p.mu / pr->p.rho),
                             (T)pr->p.C_I, pr->d_counter, st);
+    else
+      rc = launch_tau_polish<N>(m->d_tets, m->d_geo64, (const double*)y, m->E, (double*)l.tau,
+                                pr->p.mu / pr->p.rho, pr->p.C_I, pr->d_counter, st);
+  } else {
+    rc = launch_tau<T, N>(m->d_tets, geo_of<T>(m), y, m->E, l.tau, (T)(pr->p.mu / pr->p.rho),
+                          (T)pr->p.C_I, pr->d_counter, st);
+  }
   if (rc) return fail(TS_ERR_CUDA, "tau kernel launch failed");
   TS_CUDA(cudaMemsetAsync(r, 0, n * sizeof(T), st));
   TS_TRY(apply_colours<T, N>(pr, MODE_RESIDUAL, y, y, l, r, false, st));
@@ -561,6 +572,8 @@ int ts_problem_create(const ts_mesh* mesh, const ts_params* params, ts_problem**
   {
     const char* env = getenv("TSGLS_COLOURED_FP32");
     pr->fast32 = !(env && env[0] == '1');
+    const char* env2 = getenv("TSGLS_TAU_FP64_JACOBI");
+    pr->tau_exact64 = env2 && env2[0] == '1';
   }
   if (dalloc(&pr->d_dmask, (size_t)mesh->V) || dalloc(&pr->d_counter, 1)) {
     ts_problem_free(pr);
@@ -751,6 +764,7 @@ int ts_solve(ts_problem* pr, void* y_inout, const ts_solve_opts* opts, ts_solve_
     if (ser) {
       if (r_first < 0) r_first = rn;
       double dt = dt0 * std::pow(r_first / rn, o.ser);
+      if (o.dt_max > 0 && dt > o.dt_max) dt = o.dt_max;
       pr->p.dt_pseudo = dt > 1e8 * dt0 ? INFINITY : dt;
     }
     // right preconditioner: approximate inverse diagonal of the tangent

@@ -104,7 +104,11 @@ struct J32Layout {
   static constexpr int U = TAU + EPW * TS;
   static constexpr int VS = U + EPW * US;             // LIN_A: v samples at the points
   static constexpr int OUT = VS + (LINA ? EPW * US : 0);   // per lane [4*C][32]
-  static constexpr int WARP = OUT + 4 * C * 32;
+  static constexpr int GT = OUT + 4 * C * 32;                 // per lane [3][C][32]: SUPG sums (modes)
+  // per-warp stride rounded to 16 bytes: the tau block at offset 0 of every
+  // warp's workspace is written with 16-byte stores
+  static constexpr int WARP = (GT + 3 * C * 32 + 3) & ~3;
+  static_assert(TAU % 4 == 0 && TS % 4 == 0 && WARP % 4 == 0, "16-byte alignment of the tau block");
 };
 
 template <int N, int MODE>
@@ -126,6 +130,7 @@ __global__ void __launch_bounds__(32 * 6, 1)
   float* s_u = ws + L::U;
   float* s_v = ws + L::VS;
   float* s_out = ws + L::OUT;
+  float* s_gt = ws + L::GT;   // [(j*C + c)*32 + lane]
   const bool active = lane < 3 * EPW;
   const int el = active ? lane / 3 : 0, ci = active ? lane - 3 * (lane / 3) : 0;
   const int wpb = blockDim.x >> 5;
@@ -336,87 +341,95 @@ __global__ void __launch_bounds__(32 * 6, 1)
           W[j][k] = acc;
         }
     }
-    // SUPG modes, viscous, pressure and mass terms
-    float Wm[3][C];
+    // SUPG sums to modes, kept in this lane's shared rows (reusing the gradient rows)
+    __syncwarp();
 #pragma unroll
-    for (int j = 0; j < 3; ++j) inv<N>(W[j], Wm[j]);
-    float gi[3][C], pbar[C];
+    for (int j = 0; j < 3; ++j) {
+      float Wm[C];
+      inv<N>(W[j], Wm);
+#pragma unroll
+      for (int c = 0; c < C; ++c) s_gt[(j * C + c) * 32 + lane] = Wm[c];
+    }
+    // dv_ci/dx_ci (this lane's share of the divergence) and the mean pressure
+    float divc[C], pbar[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) {
+      divc[c] = 0.f;
       pbar[c] = 0.f;
-      gi[0][c] = gi[1][c] = gi[2][c] = 0.f;
     }
     if (live) {
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const float* va = v + (int64_t)node[a] * 4 * C;
-        const bool fixed = dmask[node[a]] != 0;
+      for (int b = 0; b < 4; ++b) {
+        const float* vb = v + (int64_t)node[b] * 4 * C;
+        const bool fixed = dmask[node[b]] != 0;
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-          const float x = (c == 1 || fixed) ? 0.f : va[ci * C + c];
-          gi[0][c] = fmaf(dN[a * 3 + 0], x, gi[0][c]);
-          gi[1][c] = fmaf(dN[a * 3 + 1], x, gi[1][c]);
-          gi[2][c] = fmaf(dN[a * 3 + 2], x, gi[2][c]);
-          pbar[c] += (c == 1) ? 0.f : 0.25f * va[3 * C + c];
+          const float x = (c == 1 || fixed) ? 0.f : vb[ci * C + c];
+          divc[c] = fmaf(dN[b * 3 + ci], x, divc[c]);
+          pbar[c] += (c == 1) ? 0.f : 0.25f * vb[3 * C + c];
         }
       }
     }
     const float w4 = 0.25f * vol;
-    float cont[4][C];
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-      float va_own[C];
-      {
-        const float* van = v + (int64_t)node[a] * 4 * C;
-        const bool fixed = live ? dmask[node[a]] != 0 : true;
+      // viscous term through the element stiffness: sum_b (grad N_a . grad N_b) v_b
+      float vis[C], va_own[C];
 #pragma unroll
-        for (int c = 0; c < C; ++c) va_own[c] = (!live || c == 1 || fixed) ? 0.f : van[ci * C + c];
+      for (int c = 0; c < C; ++c) {
+        vis[c] = 0.f;
+        va_own[c] = 0.f;
       }
+      if (live) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const float kab = dN[a * 3] * dN[b * 3] + dN[a * 3 + 1] * dN[b * 3 + 1] + dN[a * 3 + 2] * dN[b * 3 + 2];
+          const float* vb = v + (int64_t)node[b] * 4 * C;
+          const bool fixed = dmask[node[b]] != 0;
+#pragma unroll
+          for (int c = 0; c < C; ++c) {
+            const float x = (c == 1 || fixed) ? 0.f : vb[ci * C + c];
+            vis[c] = fmaf(kab, x, vis[c]);
+            if (b == a) va_own[c] = x;
+          }
+        }
+      }
+      float m[C], cont[C];
 #pragma unroll
       for (int c = 0; c < C; ++c) {
         if (c == 1) {
-          cont[a][c] = 0.f;
+          m[c] = 0.f;
+          cont[c] = 0.f;
           continue;
         }
-        float m = w4 * s_out[(a * C + c) * 32 + lane];
-        m += w4 * (dN[a * 3 + 0] * Wm[0][c] + dN[a * 3 + 1] * Wm[1][c] + dN[a * 3 + 2] * Wm[2][c]);
-        m += ph.mu * vol * (dN[a * 3 + 0] * gi[0][c] + dN[a * 3 + 1] * gi[1][c] + dN[a * 3 + 2] * gi[2][c]);
-        m -= dN[a * 3 + ci] * vol * pbar[c];
-        if (ph.mass_coef != 0.f) m += ph.mass_coef * vol * 0.05f * (S[c] + va_own[c]);
-        s_out[(a * C + c) * 32 + lane] = m;
+        float x = w4 * s_out[(a * C + c) * 32 + lane];
+        x += w4 * (dN[a * 3 + 0] * s_gt[(0 * C + c) * 32 + lane] + dN[a * 3 + 1] * s_gt[(1 * C + c) * 32 + lane] +
+                   dN[a * 3 + 2] * s_gt[(2 * C + c) * 32 + lane]);
+        x += ph.mu * vol * vis[c];
+        x -= dN[a * 3 + ci] * vol * pbar[c];
+        if (ph.mass_coef != 0.f) x += ph.mass_coef * vol * 0.05f * (S[c] + va_own[c]);
+        m[c] = x;
         // continuity: this lane's share of w div + (w/rho) dN_a/dx_ci sum_q Tc_ci
-        cont[a][c] = w4 * gi[ci][c] + (w4 / rho) * dN[a * 3 + ci] * sumTc[c];
+        cont[c] = w4 * divc[c] + (w4 / rho) * dN[a * 3 + ci] * sumTc[c];
       }
-    }
-    // reduce the continuity rows over the element's three lanes
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
+      // reduce the continuity row over the element's three lanes
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        const float x1 = __shfl_down_sync(0xffffffffu, cont[a][c], 1);
-        const float x2 = __shfl_down_sync(0xffffffffu, cont[a][c], 2);
-        cont[a][c] += x1 + x2;
+        const float x1 = __shfl_down_sync(0xffffffffu, cont[c], 1);
+        const float x2 = __shfl_down_sync(0xffffffffu, cont[c], 2);
+        cont[c] += x1 + x2;
       }
-    // scatter-add (vector atomics); fixed rows are skipped
-    if (live) {
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
+      // scatter-add (8-byte vector atomics); fixed rows are skipped
+      if (live) {
         float* dst = out + (int64_t)node[a] * 4 * C;
         if (!dmask[node[a]]) {
 #pragma unroll
-          for (int c = 0; c < C; c += 2) {
-            float2 val = make_float2(s_out[(a * C + c) * 32 + lane], s_out[(a * C + c + 1) * 32 + lane]);
-            if (c == 0) val.y = 0.f;
-            atomicAdd(reinterpret_cast<float2*>(dst + ci * C + c), val);
-          }
+          for (int c = 0; c < C; c += 2) atomicAdd(reinterpret_cast<float2*>(dst + ci * C + c), make_float2(m[c], m[c + 1]));
         }
         if (ci == 0) {
 #pragma unroll
-          for (int c = 0; c < C; c += 2) {
-            float2 val = make_float2(cont[a][c], cont[a][c + 1]);
-            if (c == 0) val.y = 0.f;
-            atomicAdd(reinterpret_cast<float2*>(dst + 3 * C + c), val);
-          }
+          for (int c = 0; c < C; c += 2)
+            atomicAdd(reinterpret_cast<float2*>(dst + 3 * C + c), make_float2(cont[c], cont[c + 1]));
         }
       }
     }

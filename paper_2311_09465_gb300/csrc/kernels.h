@@ -21,6 +21,12 @@ template <typename T, int N>
 int launch_tau(const int4* tets, const T* geo, const T* y, int64_t n_elem, T* tau_out, T nu,
                T C_I, unsigned* n_unconverged, cudaStream_t st);
 
+// FP64 tau from FP32 Jacobi eigenvectors plus an FP64 polish (tau.cu)
+template <int N>
+int launch_tau_polish(const int4* tets, const double* geo, const double* y, int64_t n_elem,
+                      double* tau_out, double nu, double C_I, unsigned* n_unconverged,
+                      cudaStream_t st);
+
 // One colour range [e0, e1) of the element operator (see apply.cu).
 template <typename T, int N>
 int launch_apply(int mode, const int4* tets, const T* geo, const T* v, const T* u0,

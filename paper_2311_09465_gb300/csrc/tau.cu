@@ -45,6 +45,90 @@ __device__ __forceinline__ T conv_entry(const T* a, int r, int s) {
   return ar(m - n) - ar(m + n);
 }
 
+
+// Parallel cyclic Jacobi on the symmetric NP x NP matrix M (row stride NP+1)
+// owned by a group of N lanes; rotations accumulate into V (V <- V J).
+// Round-robin ordering: in each of the NP-1 rounds the N lanes rotate N
+// disjoint pairs, rows first then columns.  Every lane of the warp must call
+// this function (it synchronises the warp); lanes with live == false only
+// take part in the synchronisation.  Returns whether this group reached
+// sum_{i<j} M_ij^2 <= tol2 * sum_i M_ii^2 within max_sweeps.
+template <typename T, int N>
+__device__ bool jacobi_group(T* M, T* Vv, int k, int g, int lane, bool live, T* red,
+                             int max_sweeps, T tol2) {
+  constexpr int NP = 2 * N, NM = 2 * N - 1, LD = NP + 1, P = NP - 1;
+  bool converged = false;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    for (int rr = 0; rr < P; ++rr) {
+      int p, qq;
+      if (k == 0) {
+        p = 0;
+        qq = 1 + rr % P;
+      } else {
+        p = 1 + (rr + k) % P;
+        qq = 1 + (rr - k + P) % P;
+      }
+      T c = 1, s = 0;
+      if (live) {
+        T app = M[p * LD + p], aqq = M[qq * LD + qq], apq = M[p * LD + qq];
+        if (apq != T(0)) {
+          T zeta = (aqq - app) / (T(2) * apq);
+          T t = T(1) / (fabs(zeta) + Real<T>::sqrt(T(1) + zeta * zeta));
+          if (zeta < T(0)) t = -t;
+          c = Real<T>::rsqrt(T(1) + t * t);
+          s = t * c;
+        }
+      }
+      __syncwarp();
+      if (live && s != T(0)) {
+        for (int j = 0; j < NP; ++j) {
+          T mp = M[p * LD + j], mq = M[qq * LD + j];
+          M[p * LD + j] = c * mp - s * mq;
+          M[qq * LD + j] = s * mp + c * mq;
+        }
+      }
+      __syncwarp();
+      if (live && s != T(0)) {
+        for (int i = 0; i < NP; ++i) {
+          T mp = M[i * LD + p], mq = M[i * LD + qq];
+          M[i * LD + p] = c * mp - s * mq;
+          M[i * LD + qq] = s * mp + c * mq;
+          T vp = Vv[i * LD + p], vq = Vv[i * LD + qq];
+          Vv[i * LD + p] = c * vp - s * vq;
+          Vv[i * LD + qq] = s * vp + c * vq;
+        }
+        M[p * LD + qq] = T(0);
+        M[qq * LD + p] = T(0);
+      }
+      __syncwarp();
+    }
+    // convergence: sum of squared off-diagonals vs squared diagonal
+    T off = 0, dg = 0;
+    if (live) {
+      for (int r = k; r < NM; r += N) {
+        dg += M[r * LD + r] * M[r * LD + r];
+        for (int s = r + 1; s < NM; ++s) off += M[r * LD + s] * M[r * LD + s];
+      }
+    }
+    red[lane] = off;
+    red[32 + lane] = dg;
+    __syncwarp();
+    bool mine = true;
+    if (live) {
+      T so = 0, sd = 0;
+      for (int j = 0; j < N; ++j) {
+        so += red[g * N + j];
+        sd += red[32 + g * N + j];
+      }
+      mine = so <= tol2 * sd;
+    }
+    __syncwarp();
+    converged = mine;
+    if (__all_sync(0xffffffffu, !live || mine)) break;
+  }
+  return converged;
+}
+
 template <int N>
 struct TauLayout {
   using D = Dims<N>;
@@ -152,77 +236,7 @@ __global__ void __launch_bounds__(128) tau_kernel(const int4* __restrict__ tets,
     }
     __syncwarp();
     // parallel cyclic Jacobi
-    constexpr int P = NP - 1;
-    bool converged = false;
-    int sweep = 0;
-    for (; sweep < max_sweeps; ++sweep) {
-      for (int rr = 0; rr < P; ++rr) {
-        int p, qq;
-        if (k == 0) {
-          p = 0;
-          qq = 1 + rr % P;
-        } else {
-          p = 1 + (rr + k) % P;
-          qq = 1 + (rr - k + P) % P;
-        }
-        T c = 1, s = 0;
-        if (live) {
-          T app = M[p * LD + p], aqq = M[qq * LD + qq], apq = M[p * LD + qq];
-          if (apq != T(0)) {
-            T zeta = (aqq - app) / (T(2) * apq);
-            T t = T(1) / (fabs(zeta) + Real<T>::sqrt(T(1) + zeta * zeta));
-            if (zeta < T(0)) t = -t;
-            c = Real<T>::rsqrt(T(1) + t * t);
-            s = t * c;
-          }
-        }
-        __syncwarp();
-        if (live && s != T(0)) {
-          for (int j = 0; j < NP; ++j) {
-            T mp = M[p * LD + j], mq = M[qq * LD + j];
-            M[p * LD + j] = c * mp - s * mq;
-            M[qq * LD + j] = s * mp + c * mq;
-          }
-        }
-        __syncwarp();
-        if (live && s != T(0)) {
-          for (int i = 0; i < NP; ++i) {
-            T mp = M[i * LD + p], mq = M[i * LD + qq];
-            M[i * LD + p] = c * mp - s * mq;
-            M[i * LD + qq] = s * mp + c * mq;
-            T vp = Vv[i * LD + p], vq = Vv[i * LD + qq];
-            Vv[i * LD + p] = c * vp - s * vq;
-            Vv[i * LD + qq] = s * vp + c * vq;
-          }
-          M[p * LD + qq] = T(0);
-          M[qq * LD + p] = T(0);
-        }
-        __syncwarp();
-      }
-      // convergence: sum of squared off-diagonals vs squared diagonal
-      T off = 0, dg = 0;
-      if (live) {
-        for (int r = k; r < NM; r += N) {
-          dg += M[r * LD + r] * M[r * LD + r];
-          for (int s = r + 1; s < NM; ++s) off += M[r * LD + s] * M[r * LD + s];
-        }
-      }
-      red[lane] = off;
-      red[32 + lane] = dg;
-      __syncwarp();
-      bool mine = true;
-      if (live) {
-        T so = 0, sd = 0;
-        for (int j = 0; j < N; ++j) {
-          so += red[g * N + j];
-          sd += red[32 + g * N + j];
-        }
-        mine = so <= tol2 * sd;
-      }
-      __syncwarp();
-      converged = mine;
-      if (__all_sync(0xffffffffu, !live || mine)) break;
-    }
+    const bool converged = jacobi_group<T, N>(M, Vv, k, g, lane, live, red, max_sweeps, tol2);
     if (live && k == 0 && !converged) atomicAdd(n_unconverged, 1u);
     // tau = V diag(lambda^{-1/2}) V^T, packed upper triangle
     if (live) {
@@ -250,12 +264,7 @@ int launch_tau(const int4* tets, const T* geo, const T* y, int64_t n_elem, T* ta
   using L = TauLayout<N>;
   const int warps = 4;
   size_t smem = (size_t)warps * L::WARP * sizeof(T);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(tau_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    attr_set = true;
-  }
+  cudaFuncSetAttribute(tau_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int64_t n_qp = n_elem * 4;
   int64_t groups = (n_qp + L::GPW - 1) / L::GPW;
   int64_t blocks = (groups + warps - 1) / warps;
@@ -268,6 +277,250 @@ int launch_tau(const int4* tets, const T* geo, const T* y, int64_t n_elem, T* ta
                                                           sweeps, tol2, n_unconverged);
   return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
+
+
+// ---------------------------------------------------------------------------
+// FP64 tau from FP32 eigenvectors.  The FP32 Jacobi gives V32 with
+// V32^T M V32 diagonal to about 1e-7 ||M||.  In FP64: one Newton-Schulz step
+// (two) make V orthonormal to FP64 rounding, B = V^T M V, and f(B) = B^{-1/2} is
+// expanded to second order around diag(B) with the Daleckii-Krein formulas
+// (Frechet derivatives of a matrix function at a diagonal matrix are
+// Hadamard-type sums with the divided differences of f).  For f = l^{-1/2}
+// with s = sqrt(l) the divided differences have cancellation-free forms
+//   f[a,b]   = -1 / (s_a s_b (s_a + s_b))
+//   f[a,b,c] = (s_a + s_b + s_c) / (s_a s_b s_c (s_a+s_b)(s_b+s_c)(s_a+s_c)),
+// which gives, with X_ik = E_ik / (s_i s_k (s_i + s_k)) and E = offdiag(B),
+//   Z = diag(1/s) - X + X D_s X + (X D_{s^2} X) ./ (s_i + s_j),
+// tau = V Z V^T, error third order in E.
+template <int N>
+struct PolishLayout {
+  static constexpr int NP = 2 * N, NM = 2 * N - 1, C = 2 * N, LD = NP + 1;
+  static constexpr int GPW = 32 / N;
+  // in doubles
+  static constexpr int CM = 0;                       // [3][NM][NM] scratch
+  static constexpr int M64 = CM + 3 * NM * NM;       // [NP][LD]
+  static constexpr int V64 = M64 + NP * LD;          // [NP][LD]
+  static constexpr int W = V64 + NP * LD;            // [3][C]
+  static constexpr int F32 = W + 3 * C;              // start of the float part
+  static constexpr int GROUP = F32 + NP * LD;        // 2 [NP][LD] float matrices = NP*LD doubles
+  static constexpr int WARP = GPW * GROUP + 64 + 32; // + double and float reduction scratch
+};
+
+template <int N>
+__global__ void __launch_bounds__(128) tau_polish_kernel(const int4* __restrict__ tets,
+                                                         const double* __restrict__ geo,
+                                                         const double* __restrict__ y,
+                                                         int64_t n_qp, double* __restrict__ tau_out,
+                                                         double nu, double C_I,
+                                                         unsigned* __restrict__ n_unconverged) {
+  using L = PolishLayout<N>;
+  constexpr int NP = L::NP, NM = L::NM, C = L::C, LD = L::LD, GPW = L::GPW;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* smem = reinterpret_cast<double*>(smem_raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane / N, k = lane - (lane / N) * N;
+  const bool in_group = g < GPW;
+  double* wbase = smem + warp * L::WARP;
+  double* base = wbase + (in_group ? g : 0) * L::GROUP;
+  double* Cm = base + L::CM;
+  double* M = base + L::M64;
+  double* Vd = base + L::V64;
+  double* w = base + L::W;
+  float* Mf = reinterpret_cast<float*>(base + L::F32);
+  float* Vf = Mf + NP * LD;
+  double* red_d = wbase + GPW * L::GROUP;
+  float* red_f = reinterpret_cast<float*>(red_d + 64);
+
+  const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t qb = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * GPW; qb < n_qp;
+       qb += warps_total * GPW) {
+    const int64_t gq = qb + g;
+    const bool live = in_group && gq < n_qp;
+    const int64_t e = live ? gq >> 2 : 0;
+    const int q = (int)(gq & 3);
+    double diff = 0;
+    if (live) {
+      const double* gg = geo + e * GEO_STRIDE + GEO_G;
+      const double gxx = gg[0], gxy = gg[1], gxz = gg[2], gyy = gg[3], gyz = gg[4], gzz = gg[5];
+      const double l00 = sqrt(gxx), l10 = gxy / l00, l20 = gxz / l00;
+      const double l11 = sqrt(gyy - l10 * l10), l21 = (gyz - l20 * l10) / l11;
+      const double l22 = sqrt(gzz - l20 * l20 - l21 * l21);
+      const double GG = gxx * gxx + gyy * gyy + gzz * gzz + 2.0 * (gxy * gxy + gxz * gxz + gyz * gyz);
+      diff = C_I * nu * nu * GG;
+      const int4 nd = tets[e];
+      const int node[4] = {nd.x, nd.y, nd.z, nd.w};
+      for (int c = k; c < C; c += N) {
+        double u[3] = {0, 0, 0};
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const double lam = qp_bary(q, a);
+          const double* ya = y + (int64_t)node[a] * 4 * C;
+#pragma unroll
+          for (int i = 0; i < 3; ++i) u[i] += lam * ya[i * C + c];
+        }
+        if (c == 1) u[0] = u[1] = u[2] = 0;
+        w[0 * C + c] = l00 * u[0] + l10 * u[1] + l20 * u[2];
+        w[1 * C + c] = l11 * u[1] + l21 * u[2];
+        w[2 * C + c] = l22 * u[2];
+      }
+    }
+    __syncwarp();
+    if (live)
+      for (int t = k; t < 3 * NM * NM; t += N) {
+        const int m = t / (NM * NM), rs = t - m * NM * NM;
+        const int r = rs / NM, s = rs - r * NM;
+        Cm[t] = conv_entry<double, N>(w + m * C, r, s);
+      }
+    __syncwarp();
+    if (live)
+      for (int t = k; t < NP * NP; t += N) {
+        const int r = t / NP, s = t - r * NP;
+        if (r > s) continue;
+        double acc = 0;
+        if (r < NM && s < NM) {
+#pragma unroll
+          for (int m = 0; m < 3; ++m) {
+            const double* cr = Cm + m * NM * NM + r * NM;
+            const double* cs = Cm + m * NM * NM + s * NM;
+            for (int j = 0; j < NM; ++j) acc += cr[j] * cs[j];
+          }
+          if (r == s) acc += diff;
+        } else if (r == s) {
+          acc = 1.0;   // decoupled dummy
+        }
+        M[r * LD + s] = acc;
+        M[s * LD + r] = acc;
+        Mf[r * LD + s] = (float)acc;
+        Mf[s * LD + r] = (float)acc;
+        Vf[r * LD + s] = (r == s) ? 1.f : 0.f;
+        Vf[s * LD + r] = (r == s) ? 1.f : 0.f;
+      }
+    __syncwarp();
+    const bool conv32 = jacobi_group<float, N>(Mf, Vf, k, g, lane, live, red_f, 12, 1e-12f);
+    if (live && k == 0 && !conv32) atomicAdd(n_unconverged, 1u);
+    // V in FP64, re-orthonormalised by two Newton-Schulz steps V <- V (3I - V^T V) / 2
+    // (the FP32 eigenvectors are orthonormal only to FP32 rounding)
+    if (live)
+      for (int t = k; t < NP * NP; t += N) Vd[(t / NP) * LD + t % NP] = (double)Vf[(t / NP) * LD + t % NP];
+    __syncwarp();
+    for (int it = 0; it < 2; ++it) {
+      if (live)
+        for (int t = k; t < NM * NM; t += N) {
+          const int r = t / NM, s = t - r * NM;
+          double acc = 0;
+          for (int i = 0; i < NM; ++i) acc += Vd[i * LD + r] * Vd[i * LD + s];
+          Cm[t] = ((r == s) ? 3.0 : 0.0) - acc;      // 3I - V^T V
+        }
+      __syncwarp();
+      if (live)
+        for (int t = k; t < NM * NM; t += N) {
+          const int r = t / NM, s = t - r * NM;
+          double acc = 0;
+          for (int j = 0; j < NM; ++j) acc += Vd[r * LD + j] * Cm[j * NM + s];
+          Cm[NM * NM + t] = 0.5 * acc;
+        }
+      __syncwarp();
+      if (live)
+        for (int t = k; t < NM * NM; t += N) Vd[(t / NM) * LD + t % NM] = Cm[NM * NM + t];
+      __syncwarp();
+    }
+    // P = M V, then B = V^T M V over the NM x NM block of M (dummy row/column unchanged)
+    if (live)
+      for (int t = k; t < NM * NM; t += N) {
+        const int r = t / NM, s = t - r * NM;
+        double acc = 0;
+        for (int j = 0; j < NM; ++j) acc += M[r * LD + j] * Vd[j * LD + s];
+        Cm[t] = acc;
+      }
+    __syncwarp();
+    if (live)
+      for (int t = k; t < NM * NM; t += N) {
+        const int r = t / NM, s = t - r * NM;
+        if (r > s) continue;
+        double acc = 0;
+        for (int i = 0; i < NM; ++i) acc += Vd[i * LD + r] * Cm[i * NM + s];
+        M[r * LD + s] = acc;
+        M[s * LD + r] = acc;
+      }
+    __syncwarp();
+    // s = sqrt(diag B) once per point (reusing the w rows: 3C >= 2 NM)
+    double* sq = w;          // [NM] sqrt(b_ii)
+    double* sq2 = w + NM;    // [NM] b_ii
+    if (live)
+      for (int i = k; i < NM; i += N) {
+        sq[i] = sqrt(M[i * LD + i]);
+        sq2[i] = M[i * LD + i];
+      }
+    __syncwarp();
+    // X_ik = E_ik / (s_i s_k (s_i + s_k)), E = offdiag B
+    if (live)
+      for (int t = k; t < NM * NM; t += N) {
+        const int r = t / NM, s = t - r * NM;
+        const double sr = sq[r], ss = sq[s];
+        Cm[t] = (r == s) ? 0.0 : M[r * LD + s] / (sr * ss * (sr + ss));
+      }
+    __syncwarp();
+    // Z = diag(1/s) - X + sum_k X_ik X_kj (s_k + s_k^2 / (s_i + s_j))   (second order)
+    if (live)
+      for (int t = k; t < NM * NM; t += N) {
+        const int r = t / NM, s = t - r * NM;
+        const double sr = sq[r], ss = sq[s];
+        const double inv_rs = 1.0 / (sr + ss);
+        double acc = 0;
+        for (int j = 0; j < NM; ++j) acc += Cm[r * NM + j] * Cm[j * NM + s] * (sq[j] + sq2[j] * inv_rs);
+        Cm[NM * NM + t] = ((r == s) ? 1.0 / sr : 0.0) - Cm[t] + acc;
+      }
+    __syncwarp();
+    // Q = Z V^T in the third scratch slot
+    if (live)
+      for (int t = k; t < NM * NM; t += N) {
+        const int r = t / NM, s = t - r * NM;
+        double acc = 0;
+        for (int j = 0; j < NM; ++j) acc += Cm[NM * NM + r * NM + j] * Vd[s * LD + j];
+        Cm[2 * NM * NM + t] = acc;
+      }
+    __syncwarp();
+    if (live) {
+      double* out = tau_out + gq * Dims<N>::NT_PAD;
+      for (int t = k; t < NM * NM; t += N) {
+        const int r = t / NM, s = t - r * NM;
+        if (r > s) continue;
+        double acc = 0;
+        for (int j = 0; j < NM; ++j) acc += Vd[r * LD + j] * Cm[2 * NM * NM + j * NM + s];
+        out[packed_index(r, s, NM)] = acc;
+      }
+      if (k == 0)
+        for (int t = Dims<N>::NT; t < Dims<N>::NT_PAD; ++t) out[t] = 0.0;
+    }
+    __syncwarp();
+  }
+}
+
+template <int N>
+int launch_tau_polish(const int4* tets, const double* geo, const double* y, int64_t n_elem,
+                      double* tau_out, double nu, double C_I, unsigned* n_unconverged,
+                      cudaStream_t st) {
+  using L = PolishLayout<N>;
+  int warps = 4;
+  while (warps > 1 && (size_t)warps * L::WARP * sizeof(double) > 200 * 1024) --warps;
+  const size_t smem = (size_t)warps * L::WARP * sizeof(double);
+  if (smem > 227 * 1024) return -6;
+  cudaFuncSetAttribute(tau_polish_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int64_t n_qp = n_elem * 4;
+  const int64_t groups = (n_qp + L::GPW - 1) / L::GPW;
+  int64_t blocks = (groups + warps - 1) / warps;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  if (blocks < 1) blocks = 1;
+  count_launches(1);
+  tau_polish_kernel<N><<<(int)blocks, warps * 32, smem, st>>>(tets, geo, y, n_qp, tau_out, nu, C_I,
+                                                              n_unconverged);
+  return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+#define TS_INST_POLISH(T, N)                                                                  \
+  template int launch_tau_polish<N>(const int4*, const double*, const double*, int64_t,      \
+                                    double*, double, double, unsigned*, cudaStream_t);
+TS_FOR_EACH_N(TS_INST_POLISH, double)
 
 #define TS_INST_TAU(T, N)                                                                 \
   template int launch_tau<T, N>(const int4*, const T*, const T*, int64_t, T*, T, T,       \

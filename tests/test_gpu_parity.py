@@ -165,3 +165,32 @@ def test_colouring_is_valid(torch):
         r2 = to_np(g.residual(to_dev(y, torch.float32)))
         np.testing.assert_array_equal(r1, r2)
     assert g.colors() >= 20
+
+
+@pytest.mark.parametrize("variant", ["paper", "lin_a"])
+def test_fp32_single_launch_matches_coloured_path(torch, variant, monkeypatch):
+    # the atomic single-launch FP32 kernel and the colour-ordered kernel agree
+    case = CASES["junction_N4"]()
+    y = _state(case, seed=10)
+    v = cases.random_state(case.mesh, case.N, seed=11)
+    out = []
+    for coloured in ("0", "1"):
+        monkeypatch.setenv("TSGLS_COLOURED_FP32", coloured)
+        g = _gls(case, variant=variant, dt=0.4)
+        g.residual(to_dev(y, torch.float32))
+        out.append(to_np(g.jvp(to_dev(v, torch.float32))))
+    assert rel_l2(out[0], out[1]) <= 2e-6
+
+
+@pytest.mark.parametrize("scale", [1.0, 30.0])
+def test_fp64_tau_polish_matches_oracle_at_high_peclet(torch, scale, monkeypatch):
+    # FP64 residual: tau from FP32 Jacobi + FP64 polish (default) and from FP64
+    # Jacobi both meet the FP64 bar, also when convection makes M ill-conditioned
+    case = CASES["pipe_N7"]()
+    y = _state(case, seed=12, scale=scale)
+    ref = op.residual(op.problem_from_case(case), y)
+    for exact in ("0", "1"):
+        monkeypatch.setenv("TSGLS_TAU_FP64_JACOBI", exact)
+        g = _gls(case)
+        got = to_np(g.residual(to_dev(y, torch.float64)))
+        assert rel_l2(got, ref) <= TOL[64], (exact, rel_l2(got, ref))

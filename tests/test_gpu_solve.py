@@ -64,9 +64,11 @@ def test_womersley_pipe_config_closed_form():
     import torch
     import paper_2311_09465_gb300 as ts
     case = cases.pipe_case(N=3, Re=100.0, Wo=5.0, amps=(1.0, 0.5, 0.25), mesh=mg.pipe(nc=4, nr=4, nz=20))
-    g = ts.GLSProblem(case, variant="lin_a")
+    # plain Newton diverges from the cold start at Re 100; pseudo-time with a
+    # step that grows as the residual falls converges in about 13 steps
+    g = ts.GLSProblem(case, variant="lin_a", dt_pseudo=0.5)
     y = to_dev(case.y0, torch.float64)
-    rep = g.solve(y, precision=64, tol=1e-8, max_steps=60)
+    rep = g.solve(y, precision=64, tol=1e-8, max_steps=40, ser=1.0)
     assert rep["r_final"] <= 1e-8
     got = to_np(y)
     ex = wo.pipe_solution(case.mesh.xyz, case.info["R"], case.info["L"], case.info["U"],
