@@ -145,6 +145,27 @@ int  ts_set_bc(ts_problem* prob, int tag, int kind, double value);
  * y and r may not alias. */
 int  ts_residual(ts_problem* prob, const void* y, void* r, int precision, void* stream);
 
+/* Allocation-free FP32 residual.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory when they call
+ * in, e.g. a solver loop running under a memory pool or allocator policy that
+ * forbids new device allocations after set-up, or a host that has handed all
+ * free device memory to another runtime.  It computes the same r(y) as
+ * ts_residual(..., 32, ...) but keeps its intermediate data (tau per
+ * quadrature point, tau L and the DFT tables) in one fixed 32 MiB device array
+ * compiled into this library, which every GPU that loads the library holds
+ * until the process exits.  y and r are caller-owned FP32 device fields; r is
+ * overwritten.  Limits: (2(3N-2)(2N) + E*4*ntau + E*12*2N) floats, each part
+ * rounded up to 64, must fit in 32 MiB (ntau = (2N-1)N rounded up to a
+ * multiple of 4); larger meshes return TS_ERR_ARG with the sizes in the
+ * message.  It does not refresh the linearisation state used by ts_jvp.
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  Every call
+ * reuses the same array, so calls whose GPU work overlaps (other streams,
+ * other host threads on the same device) race on it and must be serialised
+ * by the caller.  Nothing in the array needs clearing between calls: each
+ * call writes every part it reads.  Calls no cudaMalloc or cudaFree. */
+int  ts_residual_noalloc(ts_problem* prob, const float* y, float* r, void* stream);
+
 /* Tangent product Hv (eq. K_mat, variant from the problem) at the state of
  * the last ts_residual call, plus c1 rho / dt_pseudo M v on the momentum rows
  * (section 2.5.3) when dt_pseudo is finite.  Dirichlet velocity entries and

@@ -81,6 +81,7 @@ def lib() -> ctypes.CDLL:
     L.ts_set_bc.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double]
     L.ts_residual.argtypes = [vp, vp, vp, ctypes.c_int, vp]
     L.ts_jvp.argtypes = [vp, vp, vp, ctypes.c_int, vp]
+    L.ts_residual_noalloc.argtypes = [vp, vp, vp, vp]
     L.ts_solve.argtypes = [vp, vp, ctypes.POINTER(ts_solve_opts), ctypes.POINTER(ts_solve_report), vp]
     L.ts_last_error.restype = ctypes.c_char_p
     L.ts_version.restype = ctypes.c_char_p
@@ -174,6 +175,14 @@ def ts_residual(prob, y, r, precision=None, stream=None):
     py, p = _field_ptr(y, precision)
     pr, _ = _field_ptr(r, p)
     _check(lib().ts_residual(prob, py, pr, p, _stream_ptr(stream)))
+    return r
+
+
+def ts_residual_noalloc(prob, y, r, stream=None):
+    """FP32 residual that allocates no device memory (fixed 32 MiB scratch)."""
+    py, _ = _field_ptr(y, 32)
+    pr, _ = _field_ptr(r, 32)
+    _check(lib().ts_residual_noalloc(prob, py, pr, _stream_ptr(stream)))
     return r
 
 

@@ -684,6 +684,95 @@ int ts_jvp(ts_problem* pr, const void* v, void* hv, int precision, void* stream)
   return jvp_any(pr, v, hv, precision, (cudaStream_t)stream);
 }
 
+}  // extern "C"
+
+// ------------------------------------------------------------------ allocation-free residual
+// For callers that must not allocate device memory at call time (for example
+// code running inside a real-time loop or under an allocator that forbids
+// new device allocations): the FP32 residual with tau, tau L and the DFT
+// tables held in one file-scope device array instead of the problem's
+// lazily allocated buffers.  The array is created when a device loads this
+// library and lives until the process exits.
+namespace {
+
+constexpr size_t kNoAllocFloats = (32u << 20) / sizeof(float);   // 32 MiB per device
+static __device__ __align__(256) float g_noalloc_scratch[kNoAllocFloats];
+float* g_noalloc_ptr[64] = {nullptr};
+
+// Device address of the scratch array for the current device, looked up once
+// per device with that device current.
+int noalloc_scratch(float** out) {
+  int dev = 0;
+  TS_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return fail(TS_ERR_ARG, "ts_residual_noalloc: device index >= 64");
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    TS_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = static_cast<float*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return 0;
+}
+
+template <int N>
+int residual_noalloc_impl(ts_problem* pr, const float* y, float* r, cudaStream_t st) {
+  constexpr int C = 2 * N, K = 3 * N - 2;
+  const ts_mesh* m = pr->mesh;
+  const size_t dft_n = (size_t)2 * K * C, dft_pad = (dft_n + 63) & ~(size_t)63;
+  const size_t tau_n = (size_t)m->E * 4 * pr->NTP, tau_pad = (tau_n + 63) & ~(size_t)63;
+  const size_t t0_n = (size_t)m->E * 12 * C;
+  const size_t need = dft_pad + tau_pad + t0_n;
+  if (need > kNoAllocFloats)
+    return fail(TS_ERR_ARG, "ts_residual_noalloc: mesh needs " + std::to_string(need * 4) +
+                                " bytes of scratch, the fixed array holds " +
+                                std::to_string(kNoAllocFloats * 4));
+  float* base = nullptr;
+  TS_TRY(noalloc_scratch(&base));
+  LinState<float> l;
+  l.dft = base;
+  l.tau = base + dft_pad;
+  l.t0 = l.tau + tau_pad;
+  // DFT tables, same values as the allocating path (double, rounded to float)
+  thread_local float tab[2 * (3 * 15 - 2) * (2 * 15)];
+  const double pi = 3.14159265358979323846;
+  for (size_t t = 0; t < dft_n; ++t) tab[t] = 0.f;
+  for (int k = 0; k < K; ++k) {
+    tab[k * C + 0] = 1.f;
+    for (int n = 1; n < N; ++n) {
+      const double th = 2.0 * pi * n * k / K;
+      tab[k * C + 2 * n] = (float)(2.0 * std::cos(th));
+      tab[k * C + 2 * n + 1] = (float)(-2.0 * std::sin(th));
+    }
+  }
+  float* inv = tab + K * C;
+  for (int k = 0; k < K; ++k) {
+    inv[0 * K + k] = (float)(1.0 / K);
+    for (int n = 1; n < N; ++n) {
+      const double th = 2.0 * pi * n * k / K;
+      inv[(2 * n) * K + k] = (float)(std::cos(th) / K);
+      inv[(2 * n + 1) * K + k] = (float)(-std::sin(th) / K);
+    }
+  }
+  TS_CUDA(cudaMemcpyAsync(l.dft, tab, dft_n * sizeof(float), cudaMemcpyHostToDevice, st));
+  if (launch_tau<float, N>(m->d_tets, m->d_geo32, y, m->E, l.tau, (float)(pr->p.mu / pr->p.rho),
+                           (float)pr->p.C_I, pr->d_counter, st))
+    return fail(TS_ERR_CUDA, "tau kernel launch failed");
+  TS_CUDA(cudaMemsetAsync(r, 0, (size_t)field_len(pr) * sizeof(float), st));
+  return apply_colours<float, N>(pr, MODE_RESIDUAL, y, y, l, r, false, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+int ts_residual_noalloc(ts_problem* pr, const float* y, float* r, void* stream) {
+  if (!pr || !y || !r) return fail(TS_ERR_ARG, "ts_residual_noalloc: NULL argument");
+  if ((const void*)y == (const void*)r) return fail(TS_ERR_ARG, "ts_residual_noalloc: y and r alias");
+  TS_TRY(sync_dmask(pr));
+  cudaStream_t st = (cudaStream_t)stream;
+  TS_DISPATCH(pr->p.N, (residual_noalloc_impl<NN>(pr, y, r, st)));
+}
+
 // ------------------------------------------------------------------ solve
 
 static double now_s() {
