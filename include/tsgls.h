@@ -49,11 +49,22 @@ extern "C" {
 #define TS_BC_DIRICHLET  1   /* velocity prescribed (values carried in y)  */
 #define TS_BC_TRACTION   2   /* -p n + mu du/dn = h n with h = 0           */
 #define TS_BC_RESISTANCE 3   /* h_n = -R Q_n, Q_n = int u_n . n (per mode) */
+#define TS_BC_BACKFLOW   4   /* backflow stabilisation with coefficient beta in [0,1] */
 
 /* tangent variants for ts_jvp / ts_solve (eq. K_mat) */
 #define TS_JVP_PAPER   0   /* A, tau frozen; LS parts of G_i, D_j dropped (section 2.5.2) */
 #define TS_JVP_FROZEN  1   /* A, tau frozen; all blocks of eq. (K_mat)                    */
 #define TS_JVP_LIN_A   2   /* FROZEN + derivative of A_j (tau frozen): exact up to d tau   */
+
+/* ts_problem_option keys and values (implementation choices, not physics) */
+#define TS_OPT_TAU64        1  /* how the FP64 residual computes tau (eq. 3D-tau):          */
+#define TS_TAU64_REFINE     0  /*   FP32 Jacobi eigenvectors + FP64 refinement (default)   */
+#define TS_TAU64_DOUBLEFLOAT 1 /*   the same refinement in double-float (FP32 pair)         */
+                               /*   arithmetic: ~1e-14 cond(M) relative, several times     */
+                               /*   faster on parts with a reduced FP64 rate               */
+#define TS_TAU64_JACOBI     2  /*   FP64 Jacobi eigenpairs                                 */
+#define TS_OPT_FP32_TANGENT 2  /* FP32 tangent products: 0 single launch with vector       */
+                               /* atomics (default), 1 colour-ordered launches            */
 
 typedef struct ts_mesh ts_mesh;
 typedef struct ts_problem ts_problem;
@@ -125,6 +136,9 @@ int  ts_problem_create(const ts_mesh* mesh, const ts_params* params, ts_problem*
 void ts_problem_free(ts_problem* prob);
 /* Changes pseudo-time step and tangent variant of an existing problem. */
 int  ts_problem_set(ts_problem* prob, double dt_pseudo, int jvp_variant);
+/* Sets an implementation option (TS_OPT_*); TS_ERR_ARG for an unknown key or
+ * value.  Takes effect at the next residual evaluation. */
+int  ts_problem_option(ts_problem* prob, int key, int value);
 
 /* Assigns a boundary condition to all boundary triangles with this tag.
  * TS_BC_DIRICHLET: nodes of those triangles become Dirichlet velocity nodes;
@@ -133,6 +147,13 @@ int  ts_problem_set(ts_problem* prob, double dt_pseudo, int jvp_variant);
  *   fixed during the iterations).  Dirichlet wins over any other tag at
  *   shared nodes.
  * TS_BC_TRACTION: zero traction, nothing to add (the default).
+ * TS_BC_BACKFLOW: adds the backflow stabilisation of section 2.6 on these
+ *   Neumann faces, beta = value in [0, 1]: the residual gains
+ *   -int N_A (rho/2) beta |A_n|_- u_i with |A_n|_- = (A_n - |A_n|)/2,
+ *   A_n = A(u . n), taken by eigenpairs at the 3 points of every face; it is
+ *   zero where A_n is positive semi-definite (no backflow).  The tangent
+ *   products use |A_n|_- frozen at the last residual (like tau).  Not
+ *   available in ts_residual_noalloc.
  * TS_BC_RESISTANCE: outlet with h_n = -value * Q_n; the residual gains
  *   value * Q_n * int N_A n_i on that outlet (a rank-one coupling per mode). */
 int  ts_set_bc(ts_problem* prob, int tag, int kind, double value);

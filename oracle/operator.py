@@ -78,6 +78,7 @@ class Problem:
     C_I: float
     dmask: np.ndarray                     # [V] bool, Dirichlet velocity nodes
     outlets: list = field(default_factory=list)   # [(faces [F,3], R)]
+    backflow: list = field(default_factory=list)  # [(faces [F,3], beta)]
     dN: np.ndarray = None
     vol: np.ndarray = None
     G: np.ndarray = None
@@ -91,18 +92,19 @@ class Problem:
         return self.xyz.shape[0]
 
 
-def make_problem(xyz, tets, N, rho, mu, omega, dmask, C_I=3.0, outlets=()) -> Problem:
+def make_problem(xyz, tets, N, rho, mu, omega, dmask, C_I=3.0, outlets=(), backflow=()) -> Problem:
     dN, vol, G = tet_geometry(np.asarray(xyz, np.float64), np.asarray(tets))
     return Problem(xyz=np.asarray(xyz, np.float64), tets=np.asarray(tets, np.int64), N=N,
                    rho=rho, mu=mu, omega=omega, C_I=C_I, dmask=np.asarray(dmask, bool),
-                   outlets=list(outlets), dN=dN, vol=vol, G=G)
+                   outlets=list(outlets), backflow=list(backflow), dN=dN, vol=vol, G=G)
 
 
 def problem_from_case(case) -> Problem:
     m = case.mesh
     outlets = [(m.bfaces[m.btag == tag], R) for tag, R in case.resistance.items()]
+    backflow = [(m.bfaces[m.btag == tag], b) for tag, b in getattr(case, "backflow", {}).items()]
     return make_problem(m.xyz, m.tets, case.N, case.rho, case.mu, case.omega,
-                        case.dirichlet_mask, case.C_I, outlets)
+                        case.dirichlet_mask, case.C_I, outlets, backflow)
 
 
 def free_mask(prob: Problem) -> np.ndarray:
@@ -120,6 +122,7 @@ class Linearization:
     tau: np.ndarray            # [E',4,nm,nm]
     grad_u0: np.ndarray = None  # [E',3(i),3(j),nm] du0_i/dx_j ('lin_a' only)
     T0: np.ndarray = None       # [E',4,3,nm] tau L_i(u0, p0) ('lin_a' only)
+    Bneg: list = None           # per backflow face set: [F,3,nm,nm] |A_n|_- at each face point
 
 
 def linearize(prob: Problem, y0: np.ndarray, elems=None, tau_state=None) -> Linearization:
@@ -146,7 +149,28 @@ def linearize(prob: Problem, y0: np.ndarray, elems=None, tau_state=None) -> Line
     conv = np.einsum("eqjmn,eijn->eqim", A, grad_u0)
     L0 = prob.rho * om * uq + prob.rho * conv + grad_p0[:, None]
     T0 = np.einsum("eqmn,eqin->eqim", tau, L0)
-    return Linearization(elems=elems, A=A, tau=tau, grad_u0=grad_u0, T0=T0)
+    Bneg = [_backflow_matrices(prob, Y[:, 0:3], faces) for faces, _ in prob.backflow]
+    return Linearization(elems=elems, A=A, tau=tau, grad_u0=grad_u0, T0=T0, Bneg=Bneg)
+
+
+# 3-point rule of degree 2 on a triangle: barycentric coordinates, weights area/3
+FACE_BARY = np.array([[2 / 3, 1 / 6, 1 / 6], [1 / 6, 2 / 3, 1 / 6], [1 / 6, 1 / 6, 2 / 3]])
+
+
+def _backflow_matrices(prob: Problem, U: np.ndarray, faces: np.ndarray) -> np.ndarray:
+    """|A_n|_- = (A_n - |A_n|)/2 at every face point, A_n = A_i n_i = A(u . n) (section 2.6).
+
+    |A_n| is taken through the eigenpairs of the Hermitian A_n, as the paper
+    describes (remark 1 of section 2.6).  Returns [F, 3, nm, nm].
+    """
+    n, _ = face_normals_areas(prob.xyz, faces)
+    un = np.einsum("fi,fbim->fbm", n, U[faces])            # u . n at the face vertices
+    ung = np.einsum("gb,fbm->fgm", FACE_BARY, un)          # at the 3 face points
+    An = conv_matrix(ung)                                   # [F,3,nm,nm]
+    An = 0.5 * (An + np.conj(np.swapaxes(An, -1, -2)))
+    lam, V = np.linalg.eigh(An)
+    neg = np.minimum(lam, 0.0)
+    return np.einsum("...mk,...k,...nk->...mn", V, neg, np.conj(V))
 
 
 def _outlet_flux(prob: Problem, U: np.ndarray, faces: np.ndarray):
@@ -234,6 +258,15 @@ def apply(prob: Problem, lin: Linearization, y: np.ndarray, variant: str = "froz
         Q, w = _outlet_flux(prob, Y[:, 0:3], faces)
         contrib = R * w[:, None, :, None] * Q[None, None, None, :]    # [F,1,3,nm]
         np.add.at(Ru, faces, np.broadcast_to(contrib, (faces.shape[0], 3, 3, nm)))
+    # backflow stabilisation (section 2.6): the term (w, (rho/2) beta |A_n|_- u)_Gh
+    # on the right-hand side of eq. (NS-weak), i.e. -int N_A (rho/2) beta |A_n|_- u_i
+    for (faces, beta), B in zip(prob.backflow, lin.Bneg or []):
+        _, area = face_normals_areas(prob.xyz, faces)
+        ug = np.einsum("gb,fbim->fgim", FACE_BARY, Y[faces, 0:3])   # u at the face points
+        z = np.einsum("fgmn,fgin->fgim", B, ug)
+        contrib = -0.5 * rho * beta * (area / 3.0)[:, None, None, None, None] * \
+            np.einsum("gb,fgim->fbim", FACE_BARY, z)[:, None]       # [F,1,3(b),3(i),nm]
+        np.add.at(Ru, faces, contrib[:, 0])
     Rout = np.concatenate([Ru, Rc[:, None, :]], axis=1)    # [V,4,nm]
     if return_complex:
         return Rout

@@ -20,9 +20,12 @@ LIB_PATH = os.path.join(_HERE, "lib", "libtsgls.so")
 
 TS_OK, TS_ERR_ARG, TS_ERR_CUDA, TS_ERR_OOM, TS_ERR_NOCONV, TS_ERR_NAN, TS_ERR_UNSUPPORTED = (
     0, -1, -2, -3, -4, -5, -6)
-TS_BC_DIRICHLET, TS_BC_TRACTION, TS_BC_RESISTANCE = 1, 2, 3
+TS_BC_DIRICHLET, TS_BC_TRACTION, TS_BC_RESISTANCE, TS_BC_BACKFLOW = 1, 2, 3, 4
 TS_JVP_PAPER, TS_JVP_FROZEN, TS_JVP_LIN_A = 0, 1, 2
 VARIANTS = {"paper": TS_JVP_PAPER, "frozen": TS_JVP_FROZEN, "lin_a": TS_JVP_LIN_A}
+TS_OPT_TAU64, TS_OPT_FP32_TANGENT = 1, 2
+TS_TAU64_REFINE, TS_TAU64_DOUBLEFLOAT, TS_TAU64_JACOBI = 0, 1, 2
+TAU64 = {"refine": TS_TAU64_REFINE, "doublefloat": TS_TAU64_DOUBLEFLOAT, "jacobi": TS_TAU64_JACOBI}
 SUPPORTED_N = (1, 2, 3, 4, 5, 7, 10, 15)
 
 
@@ -79,6 +82,7 @@ def lib() -> ctypes.CDLL:
     L.ts_problem_free.restype = None
     L.ts_problem_set.argtypes = [vp, ctypes.c_double, ctypes.c_int]
     L.ts_set_bc.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double]
+    L.ts_problem_option.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     L.ts_residual.argtypes = [vp, vp, vp, ctypes.c_int, vp]
     L.ts_jvp.argtypes = [vp, vp, vp, ctypes.c_int, vp]
     L.ts_residual_noalloc.argtypes = [vp, vp, vp, vp]
@@ -167,6 +171,10 @@ def ts_problem_set(prob, dt_pseudo: float, jvp_variant: int):
     _check(lib().ts_problem_set(prob, dt_pseudo, jvp_variant))
 
 
+def ts_problem_option(prob, key: int, value: int):
+    _check(lib().ts_problem_option(prob, key, value))
+
+
 def ts_set_bc(prob, tag: int, kind: int, value: float = 0.0):
     _check(lib().ts_set_bc(prob, tag, kind, value))
 
@@ -209,7 +217,8 @@ def ts_solve(prob, y, opts: ts_solve_opts, stream=None, raise_on_noconv=True) ->
 class GLSProblem:
     """Mesh + problem handles for a seeded case (``workloads.cases.Case``)."""
 
-    def __init__(self, case, variant="lin_a", dt_pseudo=math.inf):
+    def __init__(self, case, variant="lin_a", dt_pseudo=math.inf, tau64="refine",
+                 fp32_tangent="single"):
         m = case.mesh
         self.case = case
         self.N = case.N
@@ -222,6 +231,17 @@ class GLSProblem:
             ts_set_bc(self.prob, tag, TS_BC_DIRICHLET)
         for tag, R in case.resistance.items():
             ts_set_bc(self.prob, tag, TS_BC_RESISTANCE, R)
+        for tag, beta in getattr(case, "backflow", {}).items():
+            ts_set_bc(self.prob, tag, TS_BC_BACKFLOW, beta)
+        self.option(tau64=tau64, fp32_tangent=fp32_tangent)
+
+    def option(self, tau64=None, fp32_tangent=None):
+        """tau64: "refine" | "doublefloat" | "jacobi"; fp32_tangent: "single" | "coloured"."""
+        if tau64 is not None:
+            ts_problem_option(self.prob, TS_OPT_TAU64, TAU64[tau64])
+        if fp32_tangent is not None:
+            ts_problem_option(self.prob, TS_OPT_FP32_TANGENT,
+                              {"single": 0, "coloured": 1}[fp32_tangent])
 
     def set(self, dt_pseudo=math.inf, variant="lin_a"):
         ts_problem_set(self.prob, dt_pseudo, VARIANTS[variant])

@@ -86,6 +86,8 @@ struct LinState {
   T* t0 = nullptr;      // [E][4][3][C] tau L at the state
   T* dft = nullptr;     // forward [K][C] then inverse [C][K]
   T* u0t = nullptr;     // [V][3][K] u0 velocity sampled in time (FP32 fast path)
+  T* bneg = nullptr;    // [backflow points][NT_PAD] |A_n|_- (section 2.6)
+  int64_t bneg_points = 0;
   bool valid = false;
 };
 
@@ -99,6 +101,16 @@ struct Outlet {
   float* d_w32 = nullptr;
 };
 
+struct BackflowSet {
+  int tag;
+  double beta;
+  int64_t n = 0;                 // faces
+  int64_t offset = 0;            // first point in the |A_n|_- cache
+  int32_t* d_faces = nullptr;    // [n][3] outward
+  double *d_n64 = nullptr, *d_a64 = nullptr;
+  float *d_n32 = nullptr, *d_a32 = nullptr;
+};
+
 struct ts_problem {
   const ts_mesh* mesh = nullptr;
   ts_params p{};
@@ -107,6 +119,8 @@ struct ts_problem {
   uint8_t* d_dmask = nullptr;
   bool dmask_dirty = true;
   std::vector<Outlet> outlets;
+  std::vector<BackflowSet> backflow;
+  int64_t bf_points = 0;         // 3 per backflow face
   LinState<float> l32;
   LinState<double> l64;
   unsigned* d_counter = nullptr;
@@ -117,7 +131,7 @@ struct ts_problem {
   float *d_v32 = nullptr, *d_w32 = nullptr;
   double *d_D = nullptr, *d_t = nullptr;      // preconditioner diagonal (inverted), temp
   bool fast32 = true;    // FP32 products with the single-launch kernel (jvp32.cu)
-  bool tau_exact64 = false;  // FP64 tau by FP64 Jacobi instead of FP32 Jacobi + FP64 polish
+  int tau64 = TS_TAU64_REFINE;  // how the FP64 residual computes tau
 };
 
 // ------------------------------------------------------------------ helpers
@@ -198,6 +212,8 @@ static void lin_free(LinState<T>& l) {
   dfree(l.t0);
   dfree(l.dft);
   dfree(l.u0t);
+  dfree(l.bneg);
+  l.bneg_points = 0;
   l.valid = false;
 }
 
@@ -262,6 +278,45 @@ static int apply_colours(ts_problem* pr, int mode, const T* v, const T* u0, LinS
   return 0;
 }
 
+template <typename T>
+static const T* bf_normals(const BackflowSet& b);
+template <>
+const float* bf_normals<float>(const BackflowSet& b) { return b.d_n32; }
+template <>
+const double* bf_normals<double>(const BackflowSet& b) { return b.d_n64; }
+template <typename T>
+static const T* bf_area(const BackflowSet& b);
+template <>
+const float* bf_area<float>(const BackflowSet& b) { return b.d_a32; }
+template <>
+const double* bf_area<double>(const BackflowSet& b) { return b.d_a64; }
+
+template <typename T>
+static int bneg_alloc(ts_problem* pr, LinState<T>& l) {
+  if (l.bneg_points == pr->bf_points) return 0;
+  dfree(l.bneg);
+  l.bneg_points = 0;
+  if (pr->bf_points == 0) return 0;
+  TS_TRY(dalloc(&l.bneg, (size_t)pr->bf_points * pr->NTP));
+  l.bneg_points = pr->bf_points;
+  return 0;
+}
+
+// backflow stabilisation: -int N_A (rho/2) beta |A_n|_- v_i; with_matrix
+// refreshes |A_n|_- from v (the residual), otherwise the cached one is used
+template <typename T, int N>
+static int backflow_terms(ts_problem* pr, LinState<T>& l, const T* v, bool with_matrix,
+                          int mask_input, T* out, cudaStream_t st) {
+  for (auto& b : pr->backflow) {
+    const T coef = (T)(-0.5 * pr->p.rho * b.beta);
+    int rc = launch_backflow<T, N>(b.d_faces, bf_normals<T>(b), bf_area<T>(b), b.n,
+                                   with_matrix ? v : nullptr, l.bneg + b.offset * pr->NTP, v,
+                                   pr->d_dmask, mask_input, coef, out, st);
+    if (rc) return fail(TS_ERR_CUDA, "backflow kernel launch failed");
+  }
+  return 0;
+}
+
 template <typename T, int N>
 static int residual_impl(ts_problem* pr, const T* y, T* r, cudaStream_t st) {
   const ts_mesh* m = pr->mesh;
@@ -271,9 +326,12 @@ static int residual_impl(ts_problem* pr, const T* y, T* r, cudaStream_t st) {
   TS_CUDA(cudaMemcpyAsync(l.u0, y, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
   int rc;
   if constexpr (sizeof(T) == 8) {
-    if (pr->tau_exact64)
+    if (pr->tau64 == TS_TAU64_JACOBI)
       rc = launch_tau<T, N>(m->d_tets, geo_of<T>(m), y, m->E, l.tau, (T)(pr->p.mu / pr->p.rho),
                             (T)pr->p.C_I, pr->d_counter, st);
+    else if (pr->tau64 == TS_TAU64_DOUBLEFLOAT)
+      rc = launch_tau_dd<N>(m->d_tets, m->d_geo64, (const double*)y, m->E, (double*)l.tau,
+                            pr->p.mu / pr->p.rho, pr->p.C_I, pr->d_counter, st);
     else
       rc = launch_tau_polish<N>(m->d_tets, m->d_geo64, (const double*)y, m->E, (double*)l.tau,
                                 pr->p.mu / pr->p.rho, pr->p.C_I, pr->d_counter, st);
@@ -284,6 +342,8 @@ static int residual_impl(ts_problem* pr, const T* y, T* r, cudaStream_t st) {
   if (rc) return fail(TS_ERR_CUDA, "tau kernel launch failed");
   TS_CUDA(cudaMemsetAsync(r, 0, n * sizeof(T), st));
   TS_TRY(apply_colours<T, N>(pr, MODE_RESIDUAL, y, y, l, r, false, st));
+  TS_TRY(bneg_alloc(pr, l));
+  TS_TRY(backflow_terms<T, N>(pr, l, y, true, 0, r, st));
   if constexpr (sizeof(T) == 4 && N <= J32_MAX_N) {
     if (launch_node_samples<N>((const float*)l.u0, (float*)l.u0t, m->V, st))
       return fail(TS_ERR_CUDA, "node sample kernel failed");
@@ -310,6 +370,12 @@ static int convert_lin(ts_problem* pr, LinState<D>& dst, LinState<S>& src, cudaS
     rc |= vec_cast_f2d((double*)dst.u0, (const float*)src.u0, n_u, st);
     rc |= vec_cast_f2d((double*)dst.tau, (const float*)src.tau, n_tau, st);
     rc |= vec_cast_f2d((double*)dst.t0, (const float*)src.t0, n_t0, st);
+  }
+  TS_TRY(bneg_alloc(pr, dst));
+  if (pr->bf_points > 0) {
+    const int64_t nb = pr->bf_points * pr->NTP;
+    if (sizeof(D) == 4) rc |= vec_cast_d2f((float*)dst.bneg, (const double*)src.bneg, nb, st);
+    else rc |= vec_cast_f2d((double*)dst.bneg, (const float*)src.bneg, nb, st);
   }
   if (rc) return fail(TS_ERR_CUDA, "state conversion failed");
   dst.valid = true;
@@ -349,9 +415,10 @@ static int jvp_impl(ts_problem* pr, const T* v, T* hv, cudaStream_t st) {
       if (launch_outlet<T>(o.d_nodes, outlet_w<T>(o), (int)o.nodes.size(), (T)o.R, v, pr->d_dmask, 1,
                            hv, pr->C, st))
         return fail(TS_ERR_CUDA, "outlet kernel launch failed");
-    return 0;
+    return backflow_terms<T, N>(pr, l, v, false, 1, hv, st);
   }
-  return apply_colours<T, N>(pr, mode, v, l.u0, l, hv, true, st);
+  TS_TRY(apply_colours<T, N>(pr, mode, v, l.u0, l, hv, true, st));
+  return backflow_terms<T, N>(pr, l, v, false, 1, hv, st);
 }
 
 #define TS_DISPATCH(N_, CALL)                                                   \
@@ -570,10 +637,6 @@ int ts_problem_create(const ts_mesh* mesh, const ts_params* params, ts_problem**
   pr->NTP = ((nm * (nm + 1) / 2) + 3) & ~3;
   pr->dmask.assign(mesh->V, 0);
   {
-    const char* env = getenv("TSGLS_COLOURED_FP32");
-    pr->fast32 = !(env && env[0] == '1');
-    const char* env2 = getenv("TSGLS_TAU_FP64_JACOBI");
-    pr->tau_exact64 = env2 && env2[0] == '1';
   }
   if (dalloc(&pr->d_dmask, (size_t)mesh->V) || dalloc(&pr->d_counter, 1)) {
     ts_problem_free(pr);
@@ -592,6 +655,13 @@ void ts_problem_free(ts_problem* pr) {
     dfree(o.d_nodes);
     dfree(o.d_w64);
     dfree(o.d_w32);
+  }
+  for (auto& b : pr->backflow) {
+    dfree(b.d_faces);
+    dfree(b.d_n64);
+    dfree(b.d_a64);
+    dfree(b.d_n32);
+    dfree(b.d_a32);
   }
   lin_free(pr->l32);
   lin_free(pr->l64);
@@ -616,6 +686,22 @@ int ts_problem_set(ts_problem* pr, double dt_pseudo, int jvp_variant) {
   return 0;
 }
 
+int ts_problem_option(ts_problem* pr, int key, int value) {
+  if (!pr) return fail(TS_ERR_ARG, "NULL problem");
+  if (key == TS_OPT_TAU64) {
+    if (value != TS_TAU64_REFINE && value != TS_TAU64_DOUBLEFLOAT && value != TS_TAU64_JACOBI)
+      return fail(TS_ERR_ARG, "unknown TS_OPT_TAU64 value");
+    pr->tau64 = value;
+    return 0;
+  }
+  if (key == TS_OPT_FP32_TANGENT) {
+    if (value != 0 && value != 1) return fail(TS_ERR_ARG, "TS_OPT_FP32_TANGENT takes 0 or 1");
+    pr->fast32 = value == 0;
+    return 0;
+  }
+  return fail(TS_ERR_ARG, "unknown option key");
+}
+
 int ts_set_bc(ts_problem* pr, int tag, int kind, double value) {
   if (!pr) return fail(TS_ERR_ARG, "NULL problem");
   const ts_mesh* m = pr->mesh;
@@ -627,6 +713,49 @@ int ts_set_bc(ts_problem* pr, int tag, int kind, double value) {
     return 0;
   }
   if (kind == TS_BC_TRACTION) return 0;
+  if (kind == TS_BC_BACKFLOW) {
+    if (!(value >= 0 && value <= 1)) return fail(TS_ERR_ARG, "ts_set_bc: backflow beta must be in [0, 1]");
+    BackflowSet b;
+    b.tag = tag;
+    b.beta = value;
+    std::vector<int32_t> fc;
+    std::vector<double> nn, ar;
+    for (int64_t f = 0; f < m->F; ++f) {
+      if (m->btag[f] != tag) continue;
+      const int32_t* t = &m->bfaces[3 * f];
+      const double* pa = &m->xyz[3 * t[0]];
+      double u[3], w[3], n[3];
+      for (int i = 0; i < 3; ++i) {
+        u[i] = m->xyz[3 * t[1] + i] - pa[i];
+        w[i] = m->xyz[3 * t[2] + i] - pa[i];
+      }
+      n[0] = u[1] * w[2] - u[2] * w[1];
+      n[1] = u[2] * w[0] - u[0] * w[2];
+      n[2] = u[0] * w[1] - u[1] * w[0];
+      const double len = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+      fc.insert(fc.end(), t, t + 3);
+      for (int i = 0; i < 3; ++i) nn.push_back(n[i] / len);
+      ar.push_back(0.5 * len);
+    }
+    if (fc.empty()) return fail(TS_ERR_ARG, "ts_set_bc: no boundary face carries this tag");
+    b.n = (int64_t)ar.size();
+    b.offset = pr->bf_points;
+    std::vector<float> nn32(nn.begin(), nn.end()), ar32(ar.begin(), ar.end());
+    int rc = dalloc(&b.d_faces, fc.size()) | dalloc(&b.d_n64, nn.size()) | dalloc(&b.d_a64, ar.size()) |
+             dalloc(&b.d_n32, nn.size()) | dalloc(&b.d_a32, ar.size());
+    if (rc) return TS_ERR_OOM;
+    TS_CUDA(cudaMemcpy(b.d_faces, fc.data(), fc.size() * 4, cudaMemcpyHostToDevice));
+    TS_CUDA(cudaMemcpy(b.d_n64, nn.data(), nn.size() * 8, cudaMemcpyHostToDevice));
+    TS_CUDA(cudaMemcpy(b.d_a64, ar.data(), ar.size() * 8, cudaMemcpyHostToDevice));
+    TS_CUDA(cudaMemcpy(b.d_n32, nn32.data(), nn32.size() * 4, cudaMemcpyHostToDevice));
+    TS_CUDA(cudaMemcpy(b.d_a32, ar32.data(), ar32.size() * 4, cudaMemcpyHostToDevice));
+    pr->bf_points += 3 * b.n;
+    pr->backflow.push_back(b);
+    // the cached state no longer matches the problem
+    pr->l32.valid = false;
+    pr->l64.valid = false;
+    return 0;
+  }
   if (kind != TS_BC_RESISTANCE) return fail(TS_ERR_ARG, "ts_set_bc: unknown kind");
   if (!(value >= 0)) return fail(TS_ERR_ARG, "ts_set_bc: resistance must be >= 0");
   Outlet o;
@@ -768,6 +897,8 @@ extern "C" {
 int ts_residual_noalloc(ts_problem* pr, const float* y, float* r, void* stream) {
   if (!pr || !y || !r) return fail(TS_ERR_ARG, "ts_residual_noalloc: NULL argument");
   if ((const void*)y == (const void*)r) return fail(TS_ERR_ARG, "ts_residual_noalloc: y and r alias");
+  if (!pr->backflow.empty())
+    return fail(TS_ERR_ARG, "ts_residual_noalloc: backflow stabilisation needs ts_residual");
   TS_TRY(sync_dmask(pr));
   cudaStream_t st = (cudaStream_t)stream;
   TS_DISPATCH(pr->p.N, (residual_noalloc_impl<NN>(pr, y, r, st)));

@@ -7,14 +7,13 @@
 // tau_q, T_i is sampled again for the SUPG sum sum_q w A_j T_i.
 //
 // GB300 mapping (one launch per product):
-//  * 3 lanes per element, lane i owns velocity component i: its transforms,
-//    tau matvec, Galerkin/SUPG/viscous/mass rows; 10 elements per warp.
+//  * 16 lanes per element (velocity component or pressure x quadrature
+//    point / node), two elements per warp; see the mapping note below.
 //  * The DFT matrices live in __constant__ memory and every index is a
 //    compile-time constant, so each transform is a chain of FFMAs with a
 //    constant-bank operand and register inputs.
-//  * tau for the warp's 10 consecutive elements (a contiguous block of the
-//    cache, the dominant HBM stream) is staged into shared memory with
-//    16-byte loads; the three lanes of an element read it by broadcast.
+//  * tau of a quadrature point (the dominant HBM stream) is read with 16-byte
+//    loads straight into the registers of the three lanes of that point.
 //  * u0 at the nodes is read as precomputed time samples (one transform per
 //    node per Newton step instead of one per element per product).
 //  * Results are added to the nodes with 8-byte vector atomics (red), so
@@ -92,27 +91,34 @@ __device__ __forceinline__ float om_apply(const float (&x)[2 * N], int c, float 
   return (c & 1) ? float(n) * omega * x[c - 1] : -float(n) * omega * x[c + 1];
 }
 
-constexpr int EPW = 10;   // elements per warp (3 lanes each)
+// ---------------------------------------------------------------- mapping
+// 16 lanes per element, two elements per warp.  Lane (f, q): f = lane/4
+// within the element's half warp (0..2 a velocity component, 3 the
+// pressure/continuity lane), q = lane%4 (the quadrature point in the point
+// phase, the node in the node phases).  Node-level reductions go through
+// shared memory; sums over the four points are xor butterflies over q in
+// converged code.  tau of point q sits in the registers of the three
+// velocity lanes of that point.
+constexpr int EPW = 2;    // elements per warp (16 lanes each)
 
 template <int N, int MODE>
 struct J32Layout {
-  static constexpr int C = 2 * N, K = 3 * N - 2, NTP = Dims<N>::NT_PAD;
+  static constexpr int C = 2 * N, K = 3 * N - 2;
   static constexpr bool LINA = MODE == MODE_JVP_LIN_A;
-  static constexpr int TS = 4 * NTP + 4;              // tau stride per element (16 B multiple)
-  static constexpr int US = (12 * K) | 1;             // u0 samples per element, odd stride
-  static constexpr int TAU = 0;
-  static constexpr int U = TAU + EPW * TS;
-  static constexpr int VS = U + EPW * US;             // LIN_A: v samples at the points
-  static constexpr int OUT = VS + (LINA ? EPW * US : 0);   // per lane [4*C][32]
-  static constexpr int GT = OUT + 4 * C * 32;                 // per lane [3][C][32]: SUPG sums (modes)
-  // per-warp stride rounded to 16 bytes: the tau block at offset 0 of every
-  // warp's workspace is written with 16-byte stores
-  static constexpr int WARP = (GT + 3 * C * 32 + 3) & ~3;
-  static_assert(TAU % 4 == 0 && TS % 4 == 0 && WARP % 4 == 0, "16-byte alignment of the tau block");
+  // per element (floats)
+  static constexpr int VN = 0;                       // v at the nodes [4 a][4 f][C]
+  static constexpr int GM = VN + 16 * C;             // gradients [4 f][3 j][C]
+  static constexpr int GT = GM + 12 * C;             // dv_i/dx_j samples [3 i][3 j][K]
+  static constexpr int UQ = GT + 9 * K;              // u0 samples: nodes, then points [4][3 j][K]
+  static constexpr int WM = UQ + 12 * K;             // SUPG sums, modes [3 j][3 i][C]
+  static constexpr int GU = WM + 9 * C;              // LIN_A: du0_i/dx_j samples [3 i][3 j][K]
+  static constexpr int VQ = GU + (LINA ? 9 * K : 0); // LIN_A: v at the points, samples [4 q][3 j][K]
+  static constexpr int ELEM = (VQ + (LINA ? 12 * K : 0) + 3) & ~3;
+  static constexpr int WARP = EPW * ELEM;
 };
 
 template <int N, int MODE>
-__global__ void __launch_bounds__(32 * 6, 1)
+__global__ void __launch_bounds__(128)
     jvp32_kernel(const int4* __restrict__ tets, const float* __restrict__ geo,
                  const float* __restrict__ v, const float* __restrict__ u0t,
                  const float* __restrict__ tau, const float* __restrict__ t0cache,
@@ -122,36 +128,28 @@ __global__ void __launch_bounds__(32 * 6, 1)
   using L = J32Layout<N, MODE>;
   constexpr bool PAPER = MODE == MODE_JVP_PAPER;
   constexpr bool LINA = MODE == MODE_JVP_LIN_A;
-  constexpr float QA = 0.5854101966249685f, QB = 0.1381966011250105f;
+  constexpr float QA = 0.5854101966249685f, QB = 0.1381966011250105f, QD = QA - QB;
+  constexpr unsigned FULL = 0xffffffffu;
   extern __shared__ __align__(16) float smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* ws = smem + warp * L::WARP;
-  float* s_tau = ws + L::TAU;
-  float* s_u = ws + L::U;
-  float* s_v = ws + L::VS;
-  float* s_out = ws + L::OUT;
-  float* s_gt = ws + L::GT;   // [(j*C + c)*32 + lane]
-  const bool active = lane < 3 * EPW;
-  const int el = active ? lane / 3 : 0, ci = active ? lane - 3 * (lane / 3) : 0;
+  const int slot = lane >> 4, f = (lane >> 2) & 3, q = lane & 3;
+  float* es = smem + warp * L::WARP + slot * L::ELEM;
+  float* s_vn = es + L::VN;
+  float* s_gm = es + L::GM;
+  float* s_gt = es + L::GT;
+  float* s_uq = es + L::UQ;
+  float* s_wm = es + L::WM;
+  float* s_gu = es + L::GU;
+  float* s_vq = es + L::VQ;
   const int wpb = blockDim.x >> 5;
   const float rho = ph.rho, omega = ph.omega;
 
   for (int64_t base = ((int64_t)blockIdx.x * wpb + warp) * EPW; base < n_elem;
        base += (int64_t)gridDim.x * wpb * EPW) {
-    const int nvalid = (int)((n_elem - base) < EPW ? (n_elem - base) : EPW);
-    const int64_t e = base + el;
-    const bool live = active && el < nvalid;
+    const int64_t e = base + slot;
+    const bool live = e < n_elem;
     __syncwarp();
-    // ---- stage tau of the warp's elements (contiguous in the cache)
-    {
-      const float4* src = reinterpret_cast<const float4*>(tau + base * 4 * NTP);
-      const int n4 = nvalid * NTP;   // float4 count (4*NTP floats per element)
-      for (int t = lane; t < n4; t += 32) {
-        const int ee = t / NTP, r = t - ee * NTP;
-        reinterpret_cast<float4*>(s_tau + ee * L::TS)[r] = src[t];
-      }
-    }
-    // ---- per-lane element data
+    // ---- element data (all lanes of the element read the same record)
     int node[4] = {0, 0, 0, 0};
     float dN[12], vol = 0.f;
 #pragma unroll
@@ -167,130 +165,128 @@ __global__ void __launch_bounds__(32 * 6, 1)
       for (int j = 0; j < 12; ++j) dN[j] = g[j];
       vol = g[GEO_VOL];
     }
-    // velocity component ci at the nodes (masked) and the pressure gradient
-    float S[C], dp[C];
-    float gt[3][K];   // dv_ci/dx_j on samples
+    const int my_node = q == 0 ? node[0] : q == 1 ? node[1] : q == 2 ? node[2] : node[3];
+    const bool my_fixed = live ? dmask[my_node] != 0 : true;
+    // tau of point q into registers (velocity lanes)
+    float tv[NTP];
+    if (live && f < 3) {
+      const float4* tp = reinterpret_cast<const float4*>(tau + (e * 4 + q) * NTP);
+#pragma unroll
+      for (int t = 0; t < NTP / 4; ++t) {
+        const float4 x = tp[t];
+        tv[4 * t] = x.x;
+        tv[4 * t + 1] = x.y;
+        tv[4 * t + 2] = x.z;
+        tv[4 * t + 3] = x.w;
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < NTP; ++t) tv[t] = 0.f;
+    }
+    // ---- P0: lane (f, a = q) stores field f of node a; velocity lanes store u0 samples of node a
     {
-      float gi[3][C];
+      const float* src = v + (int64_t)my_node * 4 * C + f * C;
+#pragma unroll
+      for (int c = 0; c < C; ++c)
+        s_vn[(q * 4 + f) * C + c] = (!live || c == 1 || (f < 3 && my_fixed)) ? 0.f : src[c];
+      if (f < 3) {
+        const float* us = u0t + ((int64_t)my_node * 3 + f) * K;
+#pragma unroll
+        for (int k = 0; k < K; ++k) s_uq[(q * 3 + f) * K + k] = live ? us[k] : 0.f;
+      }
+    }
+    __syncwarp();
+    // ---- P1: gradients (lane (f, j = q < 3)); u0 at the points (lane (j = f < 3, q))
+    if (q < 3) {
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        S[c] = 0.f;
-        dp[c] = 0.f;
-        gi[0][c] = gi[1][c] = gi[2][c] = 0.f;
-      }
-      if (live) {
+        float acc = 0.f;
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          const float* va = v + (int64_t)node[a] * 4 * C;
-          const bool fixed = dmask[node[a]] != 0;
-#pragma unroll
-          for (int c = 0; c < C; ++c) {
-            const float x = (c == 1 || fixed) ? 0.f : va[ci * C + c];
-            const float p = (c == 1) ? 0.f : va[3 * C + c];
-            S[c] += x;
-            gi[0][c] = fmaf(dN[a * 3 + 0], x, gi[0][c]);
-            gi[1][c] = fmaf(dN[a * 3 + 1], x, gi[1][c]);
-            gi[2][c] = fmaf(dN[a * 3 + 2], x, gi[2][c]);
-            dp[c] = fmaf(dN[a * 3 + ci], p, dp[c]);
-          }
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < 3; ++j) fwd<N>(gi[j], gt[j]);
-    }
-    // u0 component ci at the points (samples) -> shared; LIN_A also du0_ci/dx_j
-    float gu[3][K];
-    {
-      float un[4][K];
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int k = 0; k < K; ++k)
-          un[a][k] = live ? u0t[((int64_t)node[a] * 3 + ci) * K + k] : 0.f;
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-          const float s = un[0][k] + un[1][k] + un[2][k] + un[3][k];
-          if (live) s_u[el * L::US + (q * 3 + ci) * K + k] = QB * s + (QA - QB) * un[q][k];
-        }
-      if (LINA) {
-#pragma unroll
-        for (int j = 0; j < 3; ++j)
-#pragma unroll
-          for (int k = 0; k < K; ++k)
-            gu[j][k] = dN[0 * 3 + j] * un[0][k] + dN[1 * 3 + j] * un[1][k] +
-                       dN[2 * 3 + j] * un[2][k] + dN[3 * 3 + j] * un[3][k];
+        for (int a = 0; a < 4; ++a) acc = fmaf(dN[a * 3 + q], s_vn[(a * 4 + f) * C + c], acc);
+        s_gm[(f * 3 + q) * C + c] = acc;
       }
     }
-    if (LINA) {
-      // v component ci at each point, sampled -> shared
-#pragma unroll 1
-      for (int q = 0; q < 4; ++q) {
-        float vq[C], vt[K];
-        const float* vqn = v + (int64_t)node[q] * 4 * C;
-        const bool fixed = live ? dmask[node[q]] != 0 : true;
+    float uq[K];
+    if (f < 3) {
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-          const float x = (!live || c == 1 || fixed) ? 0.f : vqn[ci * C + c];
-          vq[c] = QB * S[c] + (QA - QB) * x;
-        }
-        fwd<N>(vq, vt);
-        if (live)
-#pragma unroll
-          for (int k = 0; k < K; ++k) s_v[el * L::US + (q * 3 + ci) * K + k] = vt[k];
+      for (int k = 0; k < K; ++k) {
+        const float u0k = s_uq[(0 * 3 + f) * K + k], u1k = s_uq[(1 * 3 + f) * K + k];
+        const float u2k = s_uq[(2 * 3 + f) * K + k], u3k = s_uq[(3 * 3 + f) * K + k];
+        const float uqk = s_uq[(q * 3 + f) * K + k];
+        uq[k] = QB * (u0k + u1k + u2k + u3k) + QD * uqk;
+        if (LINA && q < 3)   // du0_f/dx_q on samples
+          s_gu[(f * 3 + q) * K + k] = dN[0 * 3 + q] * u0k + dN[1 * 3 + q] * u1k + dN[2 * 3 + q] * u2k +
+                                      dN[3 * 3 + q] * u3k;
       }
     }
-    // zero the per-lane output rows
-#pragma unroll
-    for (int t = 0; t < 4 * C; ++t) s_out[t * 32 + lane] = 0.f;
     __syncwarp();
-
-    float W[3][K], sumTc[C];
+    if (f < 3) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) s_uq[(q * 3 + f) * K + k] = uq[k];   // now u0 at point q
+    }
+    // ---- P2: gradient samples (lane (i = f < 3, j = q < 3)); LIN_A: v at the points sampled
+    if (f < 3 && q < 3) {
+      float gm[C], gt[K];
+#pragma unroll
+      for (int c = 0; c < C; ++c) gm[c] = s_gm[(f * 3 + q) * C + c];
+      fwd<N>(gm, gt);
+#pragma unroll
+      for (int k = 0; k < K; ++k) s_gt[(f * 3 + q) * K + k] = gt[k];
+    }
+    if (LINA && f < 3) {
+      float vm[C], vt[K];
+#pragma unroll
+      for (int c = 0; c < C; ++c)
+        vm[c] = QB * (s_vn[(0 * 4 + f) * C + c] + s_vn[(1 * 4 + f) * C + c] + s_vn[(2 * 4 + f) * C + c] +
+                      s_vn[(3 * 4 + f) * C + c]) +
+                QD * s_vn[(q * 4 + f) * C + c];
+      fwd<N>(vm, vt);
+#pragma unroll
+      for (int k = 0; k < K; ++k) s_vq[(q * 3 + f) * K + k] = vt[k];
+    }
+    __syncwarp();
+    // ---- P3: point phase, lane (i = f < 3, q)
+    float Wp[3][K], X[C], sX[C], sT[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      X[c] = 0.f;
+      sT[c] = 0.f;
+    }
 #pragma unroll
     for (int j = 0; j < 3; ++j)
 #pragma unroll
-      for (int k = 0; k < K; ++k) W[j][k] = 0.f;
-#pragma unroll
-    for (int c = 0; c < C; ++c) sumTc[c] = 0.f;
-    const float* tq_base = s_tau + el * L::TS;
-    const float* u_base = s_u + el * L::US;
-    const float* v_base = s_v + el * L::US;
-
-#pragma unroll 1
-    for (int q = 0; q < 4; ++q) {
-      // c_ci = u0_j dv_ci/dx_j (+ v_j du0_ci/dx_j) on samples, truncated to modes
+      for (int k = 0; k < K; ++k) Wp[j][k] = 0.f;
+    if (f < 3) {
+      const int i = f;
+      // c_i = u0_j dv_i/dx_j (+ v_j du0_i/dx_j) on samples, truncated to modes
       float ct[K], cm[C];
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         float acc = 0.f;
 #pragma unroll
-        for (int j = 0; j < 3; ++j) acc = fmaf(u_base[(q * 3 + j) * K + k], gt[j][k], acc);
+        for (int j = 0; j < 3; ++j) acc = fmaf(s_uq[(q * 3 + j) * K + k], s_gt[(i * 3 + j) * K + k], acc);
         if (LINA) {
 #pragma unroll
-          for (int j = 0; j < 3; ++j) acc = fmaf(v_base[(q * 3 + j) * K + k], gu[j][k], acc);
+          for (int j = 0; j < 3; ++j) acc = fmaf(s_vq[(q * 3 + j) * K + k], s_gu[(i * 3 + j) * K + k], acc);
         }
         ct[k] = acc;
       }
       inv<N>(ct, cm);
-      // v_ci at the point (modes) and rho (Omega v + c)
-      float vq[C], G[C], Lm[C];
-      {
-        const float* vqn = v + (int64_t)node[q] * 4 * C;
-        const bool fixed = live ? dmask[node[q]] != 0 : true;
+      float G[C], Lm[C], dp[C];
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-          const float x = (!live || c == 1 || fixed) ? 0.f : vqn[ci * C + c];
-          vq[c] = QB * S[c] + (QA - QB) * x;
-        }
+      for (int c = 0; c < C; ++c) {
+        const float vq = QB * (s_vn[(0 * 4 + i) * C + c] + s_vn[(1 * 4 + i) * C + c] +
+                               s_vn[(2 * 4 + i) * C + c] + s_vn[(3 * 4 + i) * C + c]) +
+                         QD * s_vn[(q * 4 + i) * C + c];
+        X[c] = vq;   // temporarily v_i at the point
+        dp[c] = s_gm[(3 * 3 + i) * C + c];
       }
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        G[c] = (c == 1) ? 0.f : rho * (om_apply<N>(vq, c, omega) + cm[c]);
+        G[c] = (c == 1) ? 0.f : rho * (om_apply<N>(X, c, omega) + cm[c]);
         Lm[c] = PAPER ? G[c] : G[c] + dp[c];
       }
-      // T = tau_q L (packed symmetric tau in the orthonormal basis; storage scaling)
-      const float* tp = tq_base + q * NTP;
+      // T = tau_q L, Tc = tau_q dp (PAPER); packed symmetric tau, storage scaling
       float T[C], Tc[C];
 #pragma unroll
       for (int r = 0; r < NM; ++r) {
@@ -298,7 +294,7 @@ __global__ void __launch_bounds__(32 * 6, 1)
 #pragma unroll
         for (int kk = 0; kk < NM; ++kk) {
           const int a = r < kk ? r : kk, b = r < kk ? kk : r;
-          float t = tp[packed_index(a, b, NM)];
+          float t = tv[packed_index(a, b, NM)];
           if (r == 0 && kk > 0) t *= Real<float>::SQRT2;
           if (r > 0 && kk == 0) t *= Real<float>::INV_SQRT2;
           acc = fmaf(t, Lm[stor_of(kk)], acc);
@@ -310,24 +306,17 @@ __global__ void __launch_bounds__(32 * 6, 1)
       T[1] = 0.f;
       Tc[1] = 0.f;
 #pragma unroll
-      for (int c = 0; c < C; ++c) sumTc[c] += PAPER ? Tc[c] : T[c];
-      // Galerkin + (-Omega N_a) LS terms: sum_q w N_a(q) [G - Omega T]
-#pragma unroll
       for (int c = 0; c < C; ++c) {
-        const float X = G[c] - om_apply<N>(T, c, omega);
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          const float lam = (a == q) ? QA : QB;
-          s_out[(a * C + c) * 32 + lane] += lam * X;
-        }
+        sT[c] = PAPER ? Tc[c] : T[c];
+        X[c] = G[c] - om_apply<N>(T, c, omega);
       }
-      // SUPG on samples: W_j += u0_j T (+ v_j T0)
+      // SUPG products on samples: Wp_j = u0_j T (+ v_j T0)
       float Tt[K];
       fwd<N>(T, Tt);
       float T0t[K];
       if (LINA) {
         float T0m[C];
-        const float* t0p = t0cache + ((e * 4 + q) * 3 + ci) * C;
+        const float* t0p = t0cache + ((e * 4 + q) * 3 + i) * C;
 #pragma unroll
         for (int c = 0; c < C; ++c) T0m[c] = live ? t0p[c] : 0.f;
         fwd<N>(T0m, T0t);
@@ -336,102 +325,87 @@ __global__ void __launch_bounds__(32 * 6, 1)
       for (int j = 0; j < 3; ++j)
 #pragma unroll
         for (int k = 0; k < K; ++k) {
-          float acc = fmaf(u_base[(q * 3 + j) * K + k], Tt[k], W[j][k]);
-          if (LINA) acc = fmaf(v_base[(q * 3 + j) * K + k], T0t[k], acc);
-          W[j][k] = acc;
+          float acc = s_uq[(q * 3 + j) * K + k] * Tt[k];
+          if (LINA) acc = fmaf(s_vq[(q * 3 + j) * K + k], T0t[k], acc);
+          Wp[j][k] = acc;
         }
     }
-    // SUPG sums to modes, kept in this lane's shared rows (reusing the gradient rows)
-    __syncwarp();
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      float Wm[C];
-      inv<N>(W[j], Wm);
-#pragma unroll
-      for (int c = 0; c < C; ++c) s_gt[(j * C + c) * 32 + lane] = Wm[c];
-    }
-    // dv_ci/dx_ci (this lane's share of the divergence) and the mean pressure
-    float divc[C], pbar[C];
+    // ---- P4: sums over the four points (xor butterflies over q, converged code)
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-      divc[c] = 0.f;
-      pbar[c] = 0.f;
+      float x = X[c];
+      x += __shfl_xor_sync(FULL, x, 1);
+      x += __shfl_xor_sync(FULL, x, 2);
+      sX[c] = x;
+      float t = sT[c];
+      t += __shfl_xor_sync(FULL, t, 1);
+      t += __shfl_xor_sync(FULL, t, 2);
+      sT[c] = t;
     }
-    if (live) {
 #pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const float* vb = v + (int64_t)node[b] * 4 * C;
-        const bool fixed = dmask[node[b]] != 0;
+    for (int j = 0; j < 3; ++j)
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-          const float x = (c == 1 || fixed) ? 0.f : vb[ci * C + c];
-          divc[c] = fmaf(dN[b * 3 + ci], x, divc[c]);
-          pbar[c] += (c == 1) ? 0.f : 0.25f * vb[3 * C + c];
-        }
+      for (int k = 0; k < K; ++k) {
+        float w = Wp[j][k];
+        w += __shfl_xor_sync(FULL, w, 1);
+        w += __shfl_xor_sync(FULL, w, 2);
+        Wp[j][k] = w;
       }
+    // ---- P5: SUPG sums to modes, lane (i = f < 3, j = q < 3)
+    if (f < 3 && q < 3) {
+      float wt[K], wm[C];
+#pragma unroll
+      for (int k = 0; k < K; ++k) wt[k] = (q == 0) ? Wp[0][k] : (q == 1) ? Wp[1][k] : Wp[2][k];
+      inv<N>(wt, wm);
+#pragma unroll
+      for (int c = 0; c < C; ++c) s_wm[(q * 3 + f) * C + c] = wm[c];
     }
+    // continuity lanes fetch sum_q Tc_i from the velocity lanes (i, q) of their node
+    float sTi[3][C];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int c = 0; c < C; ++c) sTi[i][c] = __shfl_sync(FULL, sT[c], (lane & 16) | (i << 2) | q);
+    __syncwarp();
+    // ---- P6: node phase, lane (f, a = q): the row of field f at node a
+    const int a = q;
     const float w4 = 0.25f * vol;
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      // viscous term through the element stiffness: sum_b (grad N_a . grad N_b) v_b
-      float vis[C], va_own[C];
-#pragma unroll
-      for (int c = 0; c < C; ++c) {
-        vis[c] = 0.f;
-        va_own[c] = 0.f;
-      }
-      if (live) {
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          const float kab = dN[a * 3] * dN[b * 3] + dN[a * 3 + 1] * dN[b * 3 + 1] + dN[a * 3 + 2] * dN[b * 3 + 2];
-          const float* vb = v + (int64_t)node[b] * 4 * C;
-          const bool fixed = dmask[node[b]] != 0;
-#pragma unroll
-          for (int c = 0; c < C; ++c) {
-            const float x = (c == 1 || fixed) ? 0.f : vb[ci * C + c];
-            vis[c] = fmaf(kab, x, vis[c]);
-            if (b == a) va_own[c] = x;
-          }
-        }
-      }
-      float m[C], cont[C];
+    float row[C];
+    if (f < 3) {
+      const int i = f;
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        if (c == 1) {
-          m[c] = 0.f;
-          cont[c] = 0.f;
-          continue;
+        float m = w4 * (QB * sX[c] + QD * X[c]);                         // Galerkin + (-Omega N_a) LS
+        float supg = 0.f, visc = 0.f;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          supg = fmaf(dN[a * 3 + j], s_wm[(j * 3 + i) * C + c], supg);
+          visc = fmaf(dN[a * 3 + j], s_gm[(i * 3 + j) * C + c], visc);
         }
-        float x = w4 * s_out[(a * C + c) * 32 + lane];
-        x += w4 * (dN[a * 3 + 0] * s_gt[(0 * C + c) * 32 + lane] + dN[a * 3 + 1] * s_gt[(1 * C + c) * 32 + lane] +
-                   dN[a * 3 + 2] * s_gt[(2 * C + c) * 32 + lane]);
-        x += ph.mu * vol * vis[c];
-        x -= dN[a * 3 + ci] * vol * pbar[c];
-        if (ph.mass_coef != 0.f) x += ph.mass_coef * vol * 0.05f * (S[c] + va_own[c]);
-        m[c] = x;
-        // continuity: this lane's share of w div + (w/rho) dN_a/dx_ci sum_q Tc_ci
-        cont[c] = w4 * divc[c] + (w4 / rho) * dN[a * 3 + ci] * sumTc[c];
+        m += w4 * supg + ph.mu * vol * visc;
+        const float pbar = 0.25f * (s_vn[(0 * 4 + 3) * C + c] + s_vn[(1 * 4 + 3) * C + c] +
+                                    s_vn[(2 * 4 + 3) * C + c] + s_vn[(3 * 4 + 3) * C + c]);
+        m -= dN[a * 3 + i] * vol * pbar;
+        if (ph.mass_coef != 0.f) {
+          const float sum = s_vn[(0 * 4 + i) * C + c] + s_vn[(1 * 4 + i) * C + c] + s_vn[(2 * 4 + i) * C + c] +
+                            s_vn[(3 * 4 + i) * C + c];
+          m += ph.mass_coef * vol * 0.05f * (sum + s_vn[(a * 4 + i) * C + c]);
+        }
+        row[c] = (c == 1 || my_fixed) ? 0.f : m;
       }
-      // reduce the continuity row over the element's three lanes
+    } else {
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        const float x1 = __shfl_down_sync(0xffffffffu, cont[c], 1);
-        const float x2 = __shfl_down_sync(0xffffffffu, cont[c], 2);
-        cont[c] += x1 + x2;
+        const float div = s_gm[(0 * 3 + 0) * C + c] + s_gm[(1 * 3 + 1) * C + c] + s_gm[(2 * 3 + 2) * C + c];
+        const float ls = dN[a * 3 + 0] * sTi[0][c] + dN[a * 3 + 1] * sTi[1][c] + dN[a * 3 + 2] * sTi[2][c];
+        row[c] = (c == 1) ? 0.f : w4 * div + (w4 / rho) * ls;
       }
-      // scatter-add (8-byte vector atomics); fixed rows are skipped
-      if (live) {
-        float* dst = out + (int64_t)node[a] * 4 * C;
-        if (!dmask[node[a]]) {
+    }
+    // scatter-add: 8-byte vector atomics of this lane's row (zero rows skipped)
+    if (live && !(f < 3 && my_fixed)) {
+      float* dst = out + (int64_t)my_node * 4 * C + f * C;
 #pragma unroll
-          for (int c = 0; c < C; c += 2) atomicAdd(reinterpret_cast<float2*>(dst + ci * C + c), make_float2(m[c], m[c + 1]));
-        }
-        if (ci == 0) {
-#pragma unroll
-          for (int c = 0; c < C; c += 2)
-            atomicAdd(reinterpret_cast<float2*>(dst + 3 * C + c), make_float2(cont[c], cont[c + 1]));
-        }
-      }
+      for (int c = 0; c < C; c += 2) atomicAdd(reinterpret_cast<float2*>(dst + c), make_float2(row[c], row[c + 1]));
     }
   }
 }
@@ -468,13 +442,11 @@ static int launch_j32_mode(const int4* tets, const float* geo, const float* v, c
                            const float* tau, const float* t0, const uint8_t* dmask, float* out,
                            Phys<float> ph, int64_t n_elem, cudaStream_t st) {
   using L = J32Layout<N, MODE>;
-  int warps = 6;
-  while (warps > 1 && (size_t)warps * L::WARP * sizeof(float) > 220 * 1024) --warps;
+  const int warps = 4;
   const size_t smem = (size_t)warps * L::WARP * sizeof(float);
   cudaFuncSetAttribute(jvp32_kernel<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int64_t warps_needed = (n_elem + EPW - 1) / EPW;
-  int64_t blocks = (warps_needed + warps - 1) / warps;
-  if (blocks > 152 * 4) blocks = 152 * 4;
+  int64_t blocks = (n_elem + warps * EPW - 1) / (warps * EPW);
+  if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
   count_launches(1);
   jvp32_kernel<N, MODE><<<(int)blocks, warps * 32, smem, st>>>(tets, geo, v, u0t, tau, t0, dmask,

@@ -27,6 +27,20 @@ int launch_tau_polish(const int4* tets, const double* geo, const double* y, int6
                       double* tau_out, double nu, double C_I, unsigned* n_unconverged,
                       cudaStream_t st);
 
+// the same refinement in double-float arithmetic (tau_dd.cu)
+template <int N>
+int launch_tau_dd(const int4* tets, const double* geo, const double* y, int64_t n_elem,
+                  double* tau_out, double nu, double C_I, unsigned* n_unconverged,
+                  cudaStream_t st);
+
+// Backflow stabilisation on one Neumann face set (tau.cu): when y_for_matrix
+// is given, first |A_n|_- at the 3 points of every face into bneg; then
+// out[A][i] += coef * int N_A |A_n|_- v_i over the faces (atomics).
+template <typename T, int N>
+int launch_backflow(const int32_t* faces, const T* normals, const T* area, int64_t n_faces,
+                    const T* y_for_matrix, T* bneg, const T* v, const uint8_t* dmask, int mask_input,
+                    T coef, T* out, cudaStream_t st);
+
 // One colour range [e0, e1) of the element operator (see apply.cu).
 template <typename T, int N>
 int launch_apply(int mode, const int4* tets, const T* geo, const T* v, const T* u0,

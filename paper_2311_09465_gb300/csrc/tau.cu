@@ -13,121 +13,10 @@
 // round, one per lane), padded with a decoupled dummy row to size 2N.
 // tau = V diag(lambda^{-1/2}) V^T is written as a packed upper triangle.
 #include "common.cuh"
+#include "jacobi.cuh"
 #include "kernels.h"
 
 namespace ts {
-
-// entry (r, s) of the real symmetric convolution matrix of a (storage
-// coordinates a[0..C-1]) in the orthonormal basis (x0, sqrt2 Re, sqrt2 Im)
-template <typename T, int N>
-__device__ __forceinline__ T conv_entry(const T* a, int r, int s) {
-  auto ar = [&](int k) -> T {
-    int m = k < 0 ? -k : k;
-    return m < N ? a[2 * m] : T(0);
-  };
-  auto ai = [&](int k) -> T {
-    int m = k < 0 ? -k : k;
-    if (m >= N || m == 0) return T(0);
-    return k > 0 ? a[2 * m + 1] : -a[2 * m + 1];
-  };
-  if (r == 0 && s == 0) return a[0];
-  const T s2 = Real<T>::SQRT2;
-  if (r == 0 || s == 0) {
-    int o = r == 0 ? s : r;
-    int n = (o + 1) >> 1;
-    return (o & 1) ? s2 * ar(n) : s2 * ai(n);
-  }
-  int m = (r + 1) >> 1, n = (s + 1) >> 1;
-  bool rre = r & 1, sre = s & 1;
-  if (rre && sre) return ar(m - n) + ar(m + n);
-  if (rre && !sre) return ai(m + n) - ai(m - n);
-  if (!rre && sre) return ai(m - n) + ai(m + n);
-  return ar(m - n) - ar(m + n);
-}
-
-
-// Parallel cyclic Jacobi on the symmetric NP x NP matrix M (row stride NP+1)
-// owned by a group of N lanes; rotations accumulate into V (V <- V J).
-// Round-robin ordering: in each of the NP-1 rounds the N lanes rotate N
-// disjoint pairs, rows first then columns.  Every lane of the warp must call
-// this function (it synchronises the warp); lanes with live == false only
-// take part in the synchronisation.  Returns whether this group reached
-// sum_{i<j} M_ij^2 <= tol2 * sum_i M_ii^2 within max_sweeps.
-template <typename T, int N>
-__device__ bool jacobi_group(T* M, T* Vv, int k, int g, int lane, bool live, T* red,
-                             int max_sweeps, T tol2) {
-  constexpr int NP = 2 * N, NM = 2 * N - 1, LD = NP + 1, P = NP - 1;
-  bool converged = false;
-  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    for (int rr = 0; rr < P; ++rr) {
-      int p, qq;
-      if (k == 0) {
-        p = 0;
-        qq = 1 + rr % P;
-      } else {
-        p = 1 + (rr + k) % P;
-        qq = 1 + (rr - k + P) % P;
-      }
-      T c = 1, s = 0;
-      if (live) {
-        T app = M[p * LD + p], aqq = M[qq * LD + qq], apq = M[p * LD + qq];
-        if (apq != T(0)) {
-          T zeta = (aqq - app) / (T(2) * apq);
-          T t = T(1) / (fabs(zeta) + Real<T>::sqrt(T(1) + zeta * zeta));
-          if (zeta < T(0)) t = -t;
-          c = Real<T>::rsqrt(T(1) + t * t);
-          s = t * c;
-        }
-      }
-      __syncwarp();
-      if (live && s != T(0)) {
-        for (int j = 0; j < NP; ++j) {
-          T mp = M[p * LD + j], mq = M[qq * LD + j];
-          M[p * LD + j] = c * mp - s * mq;
-          M[qq * LD + j] = s * mp + c * mq;
-        }
-      }
-      __syncwarp();
-      if (live && s != T(0)) {
-        for (int i = 0; i < NP; ++i) {
-          T mp = M[i * LD + p], mq = M[i * LD + qq];
-          M[i * LD + p] = c * mp - s * mq;
-          M[i * LD + qq] = s * mp + c * mq;
-          T vp = Vv[i * LD + p], vq = Vv[i * LD + qq];
-          Vv[i * LD + p] = c * vp - s * vq;
-          Vv[i * LD + qq] = s * vp + c * vq;
-        }
-        M[p * LD + qq] = T(0);
-        M[qq * LD + p] = T(0);
-      }
-      __syncwarp();
-    }
-    // convergence: sum of squared off-diagonals vs squared diagonal
-    T off = 0, dg = 0;
-    if (live) {
-      for (int r = k; r < NM; r += N) {
-        dg += M[r * LD + r] * M[r * LD + r];
-        for (int s = r + 1; s < NM; ++s) off += M[r * LD + s] * M[r * LD + s];
-      }
-    }
-    red[lane] = off;
-    red[32 + lane] = dg;
-    __syncwarp();
-    bool mine = true;
-    if (live) {
-      T so = 0, sd = 0;
-      for (int j = 0; j < N; ++j) {
-        so += red[g * N + j];
-        sd += red[32 + g * N + j];
-      }
-      mine = so <= tol2 * sd;
-    }
-    __syncwarp();
-    converged = mine;
-    if (__all_sync(0xffffffffu, !live || mine)) break;
-  }
-  return converged;
-}
 
 template <int N>
 struct TauLayout {
@@ -521,6 +410,173 @@ int launch_tau_polish(const int4* tets, const double* geo, const double* y, int6
   template int launch_tau_polish<N>(const int4*, const double*, const double*, int64_t,      \
                                     double*, double, double, unsigned*, cudaStream_t);
 TS_FOR_EACH_N(TS_INST_POLISH, double)
+
+
+// ---------------------------------------------------------------------------
+// Backflow stabilisation (section 2.6): at every point of a Neumann face,
+// |A_n|_- = (A_n - |A_n|)/2 with A_n = A_i n_i = A(u . n), taken through the
+// eigenpairs of A_n (remark 1 of section 2.6), stored like tau as a packed
+// upper triangle in the orthonormal real basis.  Face points: the 3-point
+// degree-2 rule (barycentric 2/3, 1/6, 1/6), weights area/3.
+__host__ __device__ constexpr double face_bary(int g, int b) { return g == b ? 2.0 / 3.0 : 1.0 / 6.0; }
+
+template <int N>
+struct BackflowLayout {
+  static constexpr int NP = 2 * N, C = 2 * N, LD = NP + 1, GPW = 32 / N;
+  static constexpr int M = 0, V = M + NP * LD, W = V + NP * LD;
+  static constexpr int GROUP = (W + C + 1) & ~1;
+  static constexpr int WARP = GPW * GROUP + 64;
+};
+
+template <typename T, int N>
+__global__ void __launch_bounds__(128) backflow_neg_kernel(const int32_t* __restrict__ faces,
+                                                           const T* __restrict__ normals,
+                                                           const T* __restrict__ y, int64_t n_pts,
+                                                           T* __restrict__ bneg) {
+  using L = BackflowLayout<N>;
+  constexpr int NP = L::NP, NM = 2 * N - 1, C = L::C, LD = L::LD, GPW = L::GPW;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* smem = reinterpret_cast<T*>(smem_raw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane / N, k = lane - (lane / N) * N;
+  const bool in_group = g < GPW;
+  T* wbase = smem + warp * L::WARP;
+  T* base = wbase + (in_group ? g : 0) * L::GROUP;
+  T* M = base + L::M;
+  T* Vv = base + L::V;
+  T* w = base + L::W;
+  T* red = wbase + GPW * L::GROUP;
+  const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t pb = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * GPW; pb < n_pts;
+       pb += warps_total * GPW) {
+    const int64_t gp = pb + g;
+    const bool live = in_group && gp < n_pts;
+    const int64_t f = live ? gp / 3 : 0;
+    const int gq = (int)(gp - (gp / 3) * 3);
+    if (live) {
+      const T nx = normals[f * 3], ny = normals[f * 3 + 1], nz = normals[f * 3 + 2];
+      for (int c = k; c < C; c += N) {
+        T un = 0;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          const T* yb = y + (int64_t)faces[f * 3 + b] * 4 * C;
+          un += (T)face_bary(gq, b) * (nx * yb[c] + ny * yb[C + c] + nz * yb[2 * C + c]);
+        }
+        w[c] = (c == 1) ? T(0) : un;
+      }
+    }
+    __syncwarp();
+    if (live)
+      for (int t = k; t < NP * NP; t += N) {
+        const int r = t / NP, s2 = t - r * NP;
+        T val;
+        if (r < NM && s2 < NM) val = conv_entry<T, N>(w, r, s2);
+        else val = (r == s2) ? T(1) : T(0);   // decoupled dummy
+        M[r * LD + s2] = val;
+        Vv[r * LD + s2] = (r == s2) ? T(1) : T(0);
+      }
+    __syncwarp();
+    jacobi_group<T, N>(M, Vv, k, g, lane, live, red, sizeof(T) == 4 ? 12 : 20,
+                       sizeof(T) == 4 ? T(1e-12) : T(1e-28));
+    if (live) {
+      T* out = bneg + gp * Dims<N>::NT_PAD;
+      for (int t = k; t < NM * NM; t += N) {
+        const int r = t / NM, s2 = t - r * NM;
+        if (r > s2) continue;
+        T acc = 0;
+        for (int j = 0; j < NM; ++j) {
+          const T lam = M[j * LD + j];
+          if (lam < T(0)) acc += Vv[r * LD + j] * Vv[s2 * LD + j] * lam;
+        }
+        out[packed_index(r, s2, NM)] = acc;
+      }
+      if (k == 0)
+        for (int t = Dims<N>::NT; t < Dims<N>::NT_PAD; ++t) out[t] = T(0);
+    }
+    __syncwarp();
+  }
+}
+
+// out[A][i] += coef * sum_g (area/3) N_A(g) |A_n|_- u_i(g), one thread per (face, point, i)
+template <typename T, int N>
+__global__ void backflow_apply_kernel(const int32_t* __restrict__ faces, const T* __restrict__ area,
+                                      const T* __restrict__ bneg, const T* __restrict__ v,
+                                      const uint8_t* __restrict__ dmask, int mask_input, T coef,
+                                      T* __restrict__ out, int64_t n_faces) {
+  constexpr int C = 2 * N, NM = 2 * N - 1, NTP = Dims<N>::NT_PAD;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_faces * 9;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t f = t / 9;
+    const int gi = (int)(t - f * 9), g = gi / 3, i = gi - (gi / 3) * 3;
+    int nb[3];
+    T u[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) u[c] = 0;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      nb[b] = faces[f * 3 + b];
+      if (mask_input && dmask[nb[b]]) continue;
+      const T* vb = v + (int64_t)nb[b] * 4 * C + i * C;
+#pragma unroll
+      for (int c = 0; c < C; ++c) u[c] += (T)face_bary(g, b) * vb[c];
+    }
+    u[1] = 0;
+    const T* B = bneg + (f * 3 + g) * NTP;
+    T z[C];
+#pragma unroll
+    for (int r = 0; r < NM; ++r) {
+      T acc = 0;
+#pragma unroll
+      for (int kk = 0; kk < NM; ++kk) {
+        const int a = r < kk ? r : kk, b = r < kk ? kk : r;
+        T bv = B[packed_index(a, b, NM)];
+        if (r == 0 && kk > 0) bv *= Real<T>::SQRT2;
+        if (r > 0 && kk == 0) bv *= Real<T>::INV_SQRT2;
+        acc += bv * u[stor_of(kk)];
+      }
+      z[stor_of(r)] = acc;
+    }
+    const T wq = coef * area[f] / T(3);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      if (dmask[nb[b]]) continue;
+      T* dst = out + (int64_t)nb[b] * 4 * C + i * C;
+      const T s = wq * (T)face_bary(g, b);
+#pragma unroll
+      for (int c = 0; c < C; ++c)
+        if (c != 1) atomicAdd(dst + c, s * z[c]);
+    }
+  }
+}
+
+template <typename T, int N>
+int launch_backflow(const int32_t* faces, const T* normals, const T* area, int64_t n_faces,
+                    const T* y_for_matrix, T* bneg, const T* v, const uint8_t* dmask, int mask_input,
+                    T coef, T* out, cudaStream_t st) {
+  if (n_faces <= 0) return 0;
+  if (y_for_matrix) {
+    using L = BackflowLayout<N>;
+    const int warps = 4;
+    const size_t smem = (size_t)warps * L::WARP * sizeof(T);
+    cudaFuncSetAttribute(backflow_neg_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int64_t n_pts = n_faces * 3;
+    int64_t blocks = ((n_pts + L::GPW - 1) / L::GPW + warps - 1) / warps;
+    if (blocks > 152 * 32) blocks = 152 * 32;
+    count_launches(1);
+    backflow_neg_kernel<T, N><<<(int)blocks, warps * 32, smem, st>>>(faces, normals, y_for_matrix, n_pts, bneg);
+  }
+  int64_t blocks = (n_faces * 9 + 127) / 128;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  count_launches(1);
+  backflow_apply_kernel<T, N><<<(int)blocks, 128, 0, st>>>(faces, area, bneg, v, dmask, mask_input, coef, out, n_faces);
+  return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+#define TS_INST_BACKFLOW(T, N)                                                                 \
+  template int launch_backflow<T, N>(const int32_t*, const T*, const T*, int64_t, const T*, T*, \
+                                     const T*, const uint8_t*, int, T, T*, cudaStream_t);
+TS_FOR_EACH_N(TS_INST_BACKFLOW, float)
+TS_FOR_EACH_N(TS_INST_BACKFLOW, double)
 
 #define TS_INST_TAU(T, N)                                                                 \
   template int launch_tau<T, N>(const int4*, const T*, const T*, int64_t, T*, T, T,       \

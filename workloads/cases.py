@@ -36,6 +36,7 @@ class Case:
     c1: float = 1.5
     dirichlet_tags: tuple = (mg.TAG_WALL, mg.TAG_INLET1, mg.TAG_INLET2)
     resistance: dict = field(default_factory=dict)   # tag -> R
+    backflow: dict = field(default_factory=dict)     # tag -> beta (backflow stabilisation)
     y0: np.ndarray | None = None                      # [V,4,N,2] float64 initial state
     dirichlet_mask: np.ndarray | None = None          # [V] bool
     info: dict = field(default_factory=dict)
