@@ -40,7 +40,7 @@ import numpy as np
 METRIC = "GLS operator element-mode evals/s; time to 1e-8 residual, mixed vs FP64 on GB300"
 KRYLOV = 30
 N_MODES = 7
-WAVE_AMP = 0.05   # 1/n^2 waveform scale: keeps the outlets free of backflow (no backflow term built)
+WAVE_AMP = 0.05   # 1/n^2 waveform scale (the configuration fixes the decay, not the amplitude)
 SOLVE_OPTS = dict(tol=1e-8, krylov=100, eps_ls=0.05, max_matvec=1000, precond=1, ser=1.0, dt_max=8.0,
                   raise_on_noconv=False)
 
@@ -139,7 +139,7 @@ def _jvp_bytes(case, b=4):
 def _profile_traffic(kernel_src):
     """DRAM traffic per tangent product from the committed ncu summary, if still current."""
     try:
-        with open(os.path.join(ROOT, "profiles", "apply_jvp_traffic.json")) as f:
+        with open(os.path.join(ROOT, "profiles", "jvp32_traffic.json")) as f:
             d = json.load(f)
         h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
         if d.get("source_sha") == h:
@@ -300,24 +300,29 @@ def _time_to_residual(ts, torch, case, g, args):
     out = {}
     # configs[0] geometry: Womersley pipe (R 1, L 5, ~9.6k tets), N = 3, Re 100, Wo 5
     pipe = cases.pipe_case(N=3, Re=100.0, Wo=5.0, mesh=mg.pipe(nc=4, nr=4, nz=20))
-    gp = ts.GLSProblem(pipe, variant="lin_a", dt_pseudo=0.5)
     res = {}
-    for prec in (32, 64):
+    # mixed: FP32 tangent products, FP64 GMRES, outer residual with double-float tau;
+    # plain FP64: FP64 products and the FP64 tau refinement
+    for prec, tau64 in ((32, "doublefloat"), (64, "refine")):
+        gp = ts.GLSProblem(pipe, variant="lin_a", dt_pseudo=0.5, tau64=tau64)
         yy, rep = _one_solve(ts, torch, gp, pipe.y0, prec, 60)
+        rep["tau64"] = tau64
         res["mixed" if prec == 32 else "fp64"] = rep
         if prec == 32:
             y_mixed = yy
+        gp.close()
     if res["mixed"]["converged"] and res["fp64"]["converged"]:
         res["speedup_mixed_over_fp64"] = res["fp64"]["seconds"] / res["mixed"]["seconds"]
         res["field_rel_l2_mixed_vs_fp64"] = float((y_mixed - yy).norm() / yy.norm())
     res["workload"] = f"pipe, {pipe.mesh.n_tets} tets, N=3, Re 100, Wo 5"
     out["pipe"] = res
-    gp.close()
-    # the bench junction, mixed precision (the FP64 solve is ~10x slower per step; capped)
-    g.set(dt_pseudo=args.dt, variant="lin_a")
-    _, rep = _one_solve(ts, torch, g, case.y0, 32, args.solve_steps)
-    rep["workload"] = f"junction, {case.mesh.n_tets} tets, N=7, Re 500, Wo 10"
-    out["junction_mixed"] = rep
+    if args.solve_steps > 0:
+        # the bench junction, mixed precision, capped: at Re 500 this solve does not
+        # reach 1e-8 (its residual history is reported as measured)
+        g.set(dt_pseudo=args.dt, variant="lin_a")
+        _, rep = _one_solve(ts, torch, g, case.y0, 32, args.solve_steps)
+        rep["workload"] = f"junction, {case.mesh.n_tets} tets, N=7, Re 500, Wo 10"
+        out["junction_mixed"] = rep
     return out
 
 
@@ -380,7 +385,8 @@ def main():
     ap.add_argument("--impl", default="gls", choices=["gls", "reference"])
     ap.add_argument("--dt", type=float, default=0.2, help="pseudo-time step")
     ap.add_argument("--no-solve", dest="solve", action="store_false")
-    ap.add_argument("--solve-steps", type=int, default=150)
+    ap.add_argument("--solve-steps", type=int, default=0,
+                    help="also run the junction mixed solve for this many steps")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=400)
     ap.add_argument("--ref-sample", type=int, default=200)

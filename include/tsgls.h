@@ -58,10 +58,10 @@ extern "C" {
 
 /* ts_problem_option keys and values (implementation choices, not physics) */
 #define TS_OPT_TAU64        1  /* how the FP64 residual computes tau (eq. 3D-tau):          */
-#define TS_TAU64_REFINE     0  /*   FP32 Jacobi eigenvectors + FP64 refinement (default)   */
+#define TS_TAU64_REFINE     0  /*   FP32 Jacobi eigenvectors + FP64 refinement             */
 #define TS_TAU64_DOUBLEFLOAT 1 /*   the same refinement in double-float (FP32 pair)         */
-                               /*   arithmetic: ~1e-14 cond(M) relative, several times     */
-                               /*   faster on parts with a reduced FP64 rate               */
+                               /*   arithmetic (default): meets the FP64 bar, 2.4x faster  */
+                               /*   where FP64 runs at 1/64 of the FP32 rate               */
 #define TS_TAU64_JACOBI     2  /*   FP64 Jacobi eigenpairs                                 */
 #define TS_OPT_FP32_TANGENT 2  /* FP32 tangent products: 0 single launch with vector       */
                                /* atomics (default), 1 colour-ordered launches            */
@@ -204,6 +204,53 @@ int  ts_jvp(ts_problem* prob, const void* v, void* Hv, int precision, void* stre
  * the last iterate, report filled), TS_ERR_NAN on a non-finite norm. */
 int  ts_solve(ts_problem* prob, void* y_inout, const ts_solve_opts* opts,
               ts_solve_report* report, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Learned initial guess (no counterpart in the paper, whose Newton iteration
+ * starts from zero interior velocity with the Dirichlet data in place,
+ * section 2.4): y0 = ybar + Phi diag(sigma) f(x), with Phi a POD basis of
+ * solution snapshots and f a fully connected network
+ *   n_in -> hidden (tanh) x n_hidden_layers -> n_out (linear)
+ * from inflow coefficients, Re and Wo to the POD coefficients divided by
+ * their singular values.  Solves started from it iterate to the same
+ * tolerance as from the plain guess.  All buffers are row-major FP32 unless
+ * stated; X [B][n_in], targets and outputs [B][n_out]; parameters are one
+ * flat vector: for each layer W [n_out][n_in] then b [n_out].  Device
+ * pointers unless named *_host.  TS_ERR_ARG on sizes that do not match.
+ * ------------------------------------------------------------------------- */
+typedef struct ts_surrogate ts_surrogate;
+/* n_dof = length of one modal field (V * 8N).  Weights ~ U(+-1/sqrt(n_in))
+ * from seed, biases zero. */
+int  ts_surrogate_create(int n_in, int hidden, int n_hidden_layers, int n_out, int64_t n_dof,
+                         uint64_t seed, ts_surrogate** out);
+void ts_surrogate_free(ts_surrogate* sur);
+int64_t ts_surrogate_num_params(const ts_surrogate* sur);
+int  ts_surrogate_get_params(const ts_surrogate* sur, float* params_host, int64_t n);
+/* also resets the Adam state */
+int  ts_surrogate_set_params(ts_surrogate* sur, const float* params_host, int64_t n);
+/* out = f(X) for a batch of B inputs */
+int  ts_surrogate_forward(ts_surrogate* sur, const float* X, int B, float* out, void* stream);
+/* gradient of (1/2B) sum_b ||f(x_b) - t_b||^2 into grad (flat, may be NULL),
+ * the loss into *loss (may be NULL) */
+int  ts_surrogate_gradient(ts_surrogate* sur, const float* X, const float* T, int B, float* grad,
+                           double* loss, void* stream);
+/* one Adam step (beta 0.9 / 0.999, eps 1e-8, bias-corrected) with this gradient */
+int  ts_surrogate_adam(ts_surrogate* sur, const float* grad, double lr, void* stream);
+/* POD of S snapshots Y [S][n_dof] (FP64): mean, basis of rank <= n_out
+ * (eigenvalues below 1e-10 of the largest are dropped) */
+int  ts_surrogate_fit_basis(ts_surrogate* sur, const double* Y, int S, void* stream);
+/* fitted rank; singular values into sigma_host (may be NULL, else n_out long) */
+int  ts_surrogate_basis_rank(const ts_surrogate* sur, double* sigma_host);
+/* A [S][n_out] = Phi^T (y_s - ybar) / sigma (zero beyond the rank) */
+int  ts_surrogate_coefficients(ts_surrogate* sur, const double* Y, int S, float* A, void* stream);
+/* epochs of shuffled mini-batches (size batch, remainder dropped) of Adam on
+ * the POD coefficients of Y; mean batch loss per epoch into loss_hist */
+int  ts_surrogate_train(ts_surrogate* sur, const float* X_host, const double* Y, int S, int epochs,
+                        int batch, double lr, uint64_t seed, double* loss_hist, void* stream);
+/* y_inout (FP64 field of prob) <- ybar + Phi diag(sigma) f(x) on the free
+ * entries; Dirichlet velocity values and Im(mode 0) keep their input */
+int  ts_surrogate_guess(ts_surrogate* sur, ts_problem* prob, const float* x_host, double* y_inout,
+                        void* stream);
 
 /* Thread-local message describing the last error. */
 const char* ts_last_error(void);

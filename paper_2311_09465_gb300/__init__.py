@@ -87,6 +87,24 @@ def lib() -> ctypes.CDLL:
     L.ts_jvp.argtypes = [vp, vp, vp, ctypes.c_int, vp]
     L.ts_residual_noalloc.argtypes = [vp, vp, vp, vp]
     L.ts_solve.argtypes = [vp, vp, ctypes.POINTER(ts_solve_opts), ctypes.POINTER(ts_solve_report), vp]
+    fp, u64 = ctypes.POINTER(ctypes.c_float), ctypes.c_uint64
+    L.ts_surrogate_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, i64, u64,
+                                      ctypes.POINTER(vp)]
+    L.ts_surrogate_free.argtypes = [vp]
+    L.ts_surrogate_free.restype = None
+    L.ts_surrogate_num_params.argtypes = [vp]
+    L.ts_surrogate_num_params.restype = ctypes.c_int64
+    L.ts_surrogate_get_params.argtypes = [vp, fp, i64]
+    L.ts_surrogate_set_params.argtypes = [vp, fp, i64]
+    L.ts_surrogate_forward.argtypes = [vp, vp, ctypes.c_int, vp, vp]
+    L.ts_surrogate_gradient.argtypes = [vp, vp, vp, ctypes.c_int, vp, dp, vp]
+    L.ts_surrogate_adam.argtypes = [vp, vp, ctypes.c_double, vp]
+    L.ts_surrogate_fit_basis.argtypes = [vp, vp, ctypes.c_int, vp]
+    L.ts_surrogate_basis_rank.argtypes = [vp, dp]
+    L.ts_surrogate_coefficients.argtypes = [vp, vp, ctypes.c_int, vp, vp]
+    L.ts_surrogate_train.argtypes = [vp, fp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                     u64, dp, vp]
+    L.ts_surrogate_guess.argtypes = [vp, vp, fp, vp, vp]
     L.ts_last_error.restype = ctypes.c_char_p
     L.ts_version.restype = ctypes.c_char_p
     L.ts_launch_count.restype = ctypes.c_int64
@@ -217,7 +235,7 @@ def ts_solve(prob, y, opts: ts_solve_opts, stream=None, raise_on_noconv=True) ->
 class GLSProblem:
     """Mesh + problem handles for a seeded case (``workloads.cases.Case``)."""
 
-    def __init__(self, case, variant="lin_a", dt_pseudo=math.inf, tau64="refine",
+    def __init__(self, case, variant="lin_a", dt_pseudo=math.inf, tau64="doublefloat",
                  fp32_tangent="single"):
         m = case.mesh
         self.case = case
@@ -277,6 +295,171 @@ class GLSProblem:
         if getattr(self, "mesh", None):
             ts_mesh_free(self.mesh)
             self.mesh = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ learned initial guess
+
+def _fp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def ts_surrogate_create(n_in, hidden, n_hidden_layers, n_out, n_dof, seed=0):
+    h = ctypes.c_void_p()
+    _check(lib().ts_surrogate_create(n_in, hidden, n_hidden_layers, n_out, n_dof, seed, ctypes.byref(h)))
+    return h
+
+
+def ts_surrogate_free(sur):
+    lib().ts_surrogate_free(sur)
+
+
+def ts_surrogate_num_params(sur) -> int:
+    return int(lib().ts_surrogate_num_params(sur))
+
+
+def ts_surrogate_get_params(sur, out: np.ndarray):
+    _check(lib().ts_surrogate_get_params(sur, _fp(out), out.size))
+    return out
+
+
+def ts_surrogate_set_params(sur, flat: np.ndarray):
+    _check(lib().ts_surrogate_set_params(sur, _fp(flat), flat.size))
+
+
+def ts_surrogate_forward(sur, X, B, out, stream=None):
+    _check(lib().ts_surrogate_forward(sur, X.data_ptr(), B, out.data_ptr(), _stream_ptr(stream)))
+    return out
+
+
+def ts_surrogate_gradient(sur, X, T, B, grad, stream=None) -> float:
+    loss = ctypes.c_double()
+    _check(lib().ts_surrogate_gradient(sur, X.data_ptr(), T.data_ptr(), B,
+                                       None if grad is None else grad.data_ptr(), ctypes.byref(loss),
+                                       _stream_ptr(stream)))
+    return loss.value
+
+
+def ts_surrogate_adam(sur, grad, lr, stream=None):
+    _check(lib().ts_surrogate_adam(sur, grad.data_ptr(), lr, _stream_ptr(stream)))
+
+
+def ts_surrogate_fit_basis(sur, Y, S, stream=None):
+    _check(lib().ts_surrogate_fit_basis(sur, Y.data_ptr(), S, _stream_ptr(stream)))
+
+
+def ts_surrogate_basis_rank(sur, sigma: np.ndarray | None = None) -> int:
+    p = None if sigma is None else sigma.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    return int(lib().ts_surrogate_basis_rank(sur, p))
+
+
+def ts_surrogate_coefficients(sur, Y, S, A, stream=None):
+    _check(lib().ts_surrogate_coefficients(sur, Y.data_ptr(), S, A.data_ptr(), _stream_ptr(stream)))
+    return A
+
+
+def ts_surrogate_train(sur, X_host: np.ndarray, Y, S, epochs, batch, lr, seed, loss_hist: np.ndarray,
+                       stream=None):
+    _check(lib().ts_surrogate_train(sur, _fp(X_host), Y.data_ptr(), S, epochs, batch, lr, seed,
+                                    loss_hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                    _stream_ptr(stream)))
+    return loss_hist
+
+
+def ts_surrogate_guess(sur, prob, x_host: np.ndarray, y, stream=None):
+    _check(lib().ts_surrogate_guess(sur, prob, _fp(x_host), y.data_ptr(), _stream_ptr(stream)))
+    return y
+
+
+class Surrogate:
+    """POD basis + fully connected network giving a Newton initial guess (ts_surrogate_*)."""
+
+    def __init__(self, n_in, hidden, n_hidden_layers, n_out, n_dof, seed=0):
+        self.h = ts_surrogate_create(n_in, hidden, n_hidden_layers, n_out, n_dof, seed)
+        self.n_in, self.n_out, self.n_dof = n_in, n_out, n_dof
+        self.sizes = [n_in] + [hidden] * n_hidden_layers + [n_out]
+
+    @property
+    def n_params(self) -> int:
+        return int(lib().ts_surrogate_num_params(self.h))
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.n_params, dtype=np.float32)
+        _check(lib().ts_surrogate_get_params(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), out.size))
+        return out
+
+    def set_params(self, flat):
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        _check(lib().ts_surrogate_set_params(self.h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), a.size))
+
+    def layers(self, flat=None):
+        """[(W [out][in], b [out])] views of a flat parameter vector."""
+        flat = self.get_params() if flat is None else flat
+        out, off = [], 0
+        for n_in, n_out in zip(self.sizes[:-1], self.sizes[1:]):
+            W = flat[off: off + n_in * n_out].reshape(n_out, n_in)
+            off += n_in * n_out
+            b = flat[off: off + n_out]
+            off += n_out
+            out.append((W, b))
+        return out
+
+    def forward(self, X, stream=None):
+        import torch
+        X = X.contiguous()
+        out = torch.empty((X.shape[0], self.n_out), dtype=torch.float32, device=X.device)
+        _check(lib().ts_surrogate_forward(self.h, X.data_ptr(), X.shape[0], out.data_ptr(), _stream_ptr(stream)))
+        return out
+
+    def gradient(self, X, T, stream=None):
+        import torch
+        g = torch.empty(self.n_params, dtype=torch.float32, device=X.device)
+        loss = ctypes.c_double()
+        _check(lib().ts_surrogate_gradient(self.h, X.contiguous().data_ptr(), T.contiguous().data_ptr(),
+                                           X.shape[0], g.data_ptr(), ctypes.byref(loss), _stream_ptr(stream)))
+        return loss.value, g
+
+    def adam(self, grad, lr, stream=None):
+        _check(lib().ts_surrogate_adam(self.h, grad.data_ptr(), lr, _stream_ptr(stream)))
+
+    def fit_basis(self, Y, stream=None):
+        """Y: CUDA float64 [S][n_dof] snapshots."""
+        _check(lib().ts_surrogate_fit_basis(self.h, Y.contiguous().data_ptr(), Y.shape[0], _stream_ptr(stream)))
+        sig = np.zeros(self.n_out)
+        k = lib().ts_surrogate_basis_rank(self.h, sig.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        return sig[:k]
+
+    def coefficients(self, Y, stream=None):
+        import torch
+        A = torch.empty((Y.shape[0], self.n_out), dtype=torch.float32, device=Y.device)
+        _check(lib().ts_surrogate_coefficients(self.h, Y.contiguous().data_ptr(), Y.shape[0], A.data_ptr(),
+                                               _stream_ptr(stream)))
+        return A
+
+    def train(self, X_host, Y, epochs, batch, lr, seed=0, stream=None):
+        X = np.ascontiguousarray(X_host, dtype=np.float32)
+        hist = np.zeros(epochs)
+        _check(lib().ts_surrogate_train(self.h, X.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                        Y.contiguous().data_ptr(), X.shape[0], epochs, batch, lr, seed,
+                                        hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _stream_ptr(stream)))
+        return hist
+
+    def guess(self, problem, x, y, stream=None):
+        """y (CUDA float64 field of ``problem``, a GLSProblem) <- surrogate on its free entries."""
+        xx = np.ascontiguousarray(x, dtype=np.float32)
+        _check(lib().ts_surrogate_guess(self.h, problem.prob, xx.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                        y.data_ptr(), _stream_ptr(stream)))
+        return y
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ts_surrogate_free(self.h)
+            self.h = None
 
     def __del__(self):
         try:

@@ -11,51 +11,21 @@
 #include <vector>
 
 #include "../../include/tsgls.h"
+#include "abi_util.h"
 #include "kernels.h"
 
 using namespace ts;
 
-namespace {
-
+namespace ts {
 thread_local std::string g_last_error;
 
 int fail(int code, const std::string& msg) {
   g_last_error = msg;
   return code;
 }
+}  // namespace ts
 
-#define TS_CUDA(call)                                                                   \
-  do {                                                                                  \
-    cudaError_t err__ = (call);                                                         \
-    if (err__ != cudaSuccess)                                                           \
-      return fail(err__ == cudaErrorMemoryAllocation ? TS_ERR_OOM : TS_ERR_CUDA,        \
-                  std::string(#call) + ": " + cudaGetErrorString(err__));               \
-  } while (0)
-
-#define TS_TRY(...)               \
-  do {                            \
-    int rc__ = (__VA_ARGS__);     \
-    if (rc__ != 0) return rc__;   \
-  } while (0)
-
-template <typename T>
-int dalloc(T** p, size_t count) {
-  *p = nullptr;
-  if (count == 0) count = 1;
-  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
-  if (e != cudaSuccess) {
-    *p = nullptr;
-    return fail(e == cudaErrorMemoryAllocation ? TS_ERR_OOM : TS_ERR_CUDA,
-                std::string("cudaMalloc: ") + cudaGetErrorString(e));
-  }
-  return 0;
-}
-
-template <typename T>
-void dfree(T*& p) {
-  if (p) cudaFree(p);
-  p = nullptr;
-}
+namespace {
 
 bool n_supported(int N) {
   const int list[] = {TS_N_LIST};
@@ -131,7 +101,7 @@ struct ts_problem {
   float *d_v32 = nullptr, *d_w32 = nullptr;
   double *d_D = nullptr, *d_t = nullptr;      // preconditioner diagonal (inverted), temp
   bool fast32 = true;    // FP32 products with the single-launch kernel (jvp32.cu)
-  int tau64 = TS_TAU64_REFINE;  // how the FP64 residual computes tau
+  int tau64 = TS_TAU64_DOUBLEFLOAT;  // how the FP64 residual computes tau
 };
 
 // ------------------------------------------------------------------ helpers
@@ -451,6 +421,17 @@ static int jvp_any(ts_problem* pr, const void* v, void* hv, int precision, cudaS
 }
 
 // ------------------------------------------------------------------ C ABI
+
+namespace ts {
+// the problem's Dirichlet mask on the device, storage coordinates per field, field length
+int problem_fixed_mask(ts_problem* pr, const uint8_t** dmask, int* C, int64_t* n) {
+  TS_TRY(sync_dmask(pr));
+  *dmask = pr->d_dmask;
+  *C = pr->C;
+  *n = field_len(pr);
+  return 0;
+}
+}  // namespace ts
 
 extern "C" {
 

@@ -117,23 +117,44 @@ struct J32Layout {
   static constexpr int WARP = EPW * ELEM;
 };
 
+// One instance's operands of a tangent product (also the per-instance entry
+// of the batched launch).
+struct J32Inst {
+  const int4* tets;
+  const float* geo;
+  const float* v;
+  const float* u0t;
+  const float* tau;
+  const float* t0cache;
+  const uint8_t* dmask;
+  float* out;
+  Phys<float> ph;
+  int64_t n_elem;
+  int N;
+};
+
+// The EPW elements base, base + 1 of instance I on one warp; wsm is the
+// warp's shared-memory region (J32Layout<N, MODE>::WARP floats).
 template <int N, int MODE>
-__global__ void __launch_bounds__(128)
-    jvp32_kernel(const int4* __restrict__ tets, const float* __restrict__ geo,
-                 const float* __restrict__ v, const float* __restrict__ u0t,
-                 const float* __restrict__ tau, const float* __restrict__ t0cache,
-                 const uint8_t* __restrict__ dmask, float* __restrict__ out, Phys<float> ph,
-                 int64_t n_elem) {
+__device__ __forceinline__ void j32_pass(const J32Inst& I, int64_t base, float* wsm, int lane) {
   constexpr int C = 2 * N, K = 3 * N - 2, NM = 2 * N - 1, NTP = Dims<N>::NT_PAD;
   using L = J32Layout<N, MODE>;
   constexpr bool PAPER = MODE == MODE_JVP_PAPER;
   constexpr bool LINA = MODE == MODE_JVP_LIN_A;
   constexpr float QA = 0.5854101966249685f, QB = 0.1381966011250105f, QD = QA - QB;
   constexpr unsigned FULL = 0xffffffffu;
-  extern __shared__ __align__(16) float smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int4* __restrict__ tets = I.tets;
+  const float* __restrict__ geo = I.geo;
+  const float* __restrict__ v = I.v;
+  const float* __restrict__ u0t = I.u0t;
+  const float* __restrict__ tau = I.tau;
+  const float* __restrict__ t0cache = I.t0cache;
+  const uint8_t* __restrict__ dmask = I.dmask;
+  float* __restrict__ out = I.out;
+  const Phys<float>& ph = I.ph;
+  const int64_t n_elem = I.n_elem;
   const int slot = lane >> 4, f = (lane >> 2) & 3, q = lane & 3;
-  float* es = smem + warp * L::WARP + slot * L::ELEM;
+  float* es = wsm + slot * L::ELEM;
   float* s_vn = es + L::VN;
   float* s_gm = es + L::GM;
   float* s_gt = es + L::GT;
@@ -141,11 +162,8 @@ __global__ void __launch_bounds__(128)
   float* s_wm = es + L::WM;
   float* s_gu = es + L::GU;
   float* s_vq = es + L::VQ;
-  const int wpb = blockDim.x >> 5;
   const float rho = ph.rho, omega = ph.omega;
-
-  for (int64_t base = ((int64_t)blockIdx.x * wpb + warp) * EPW; base < n_elem;
-       base += (int64_t)gridDim.x * wpb * EPW) {
+  {
     const int64_t e = base + slot;
     const bool live = e < n_elem;
     __syncwarp();
@@ -410,6 +428,17 @@ __global__ void __launch_bounds__(128)
   }
 }
 
+template <int N, int MODE>
+__global__ void __launch_bounds__(128) jvp32_kernel(J32Inst I) {
+  using L = J32Layout<N, MODE>;
+  extern __shared__ __align__(16) float smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  for (int64_t base = ((int64_t)blockIdx.x * wpb + warp) * EPW; base < I.n_elem;
+       base += (int64_t)gridDim.x * wpb * EPW)
+    j32_pass<N, MODE>(I, base, smem + warp * L::WARP, lane);
+}
+
 // u0 at the nodes sampled in time: u0t[V][3][K]
 template <int N>
 __global__ void node_samples_kernel(const float* __restrict__ u0, float* __restrict__ u0t,
@@ -449,8 +478,8 @@ static int launch_j32_mode(const int4* tets, const float* geo, const float* v, c
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
   count_launches(1);
-  jvp32_kernel<N, MODE><<<(int)blocks, warps * 32, smem, st>>>(tets, geo, v, u0t, tau, t0, dmask,
-                                                               out, ph, n_elem);
+  J32Inst I{tets, geo, v, u0t, tau, t0, dmask, out, ph, n_elem, N};
+  jvp32_kernel<N, MODE><<<(int)blocks, warps * 32, smem, st>>>(I);
   return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
