@@ -316,6 +316,8 @@ def _time_to_residual(ts, torch, case, g, args):
         res["field_rel_l2_mixed_vs_fp64"] = float((y_mixed - yy).norm() / yy.norm())
     res["workload"] = f"pipe, {pipe.mesh.n_tets} tets, N=3, Re 100, Wo 5"
     out["pipe"] = res
+    out["batched"] = _batched_ttr(ts, torch)
+    out["surrogate"] = _surrogate_ttr(ts, torch)
     if args.solve_steps > 0:
         # the bench junction, mixed precision, capped: at Re 500 this solve does not
         # reach 1e-8 (its residual history is reported as measured)
@@ -324,6 +326,123 @@ def _time_to_residual(ts, torch, case, g, args):
         rep["workload"] = f"junction, {case.mesh.n_tets} tets, N=7, Re 500, Wo 10"
         out["junction_mixed"] = rep
     return out
+
+
+def _pipe_family(rng, n, meshes):
+    """Seeded pulsatile pipe instances: uneven meshes, N in {3, 5, 7}, Re ~ U(60, 140)."""
+    from workloads import cases
+    out = []
+    for i in range(n):
+        N = (3, 5, 7)[i % 3]
+        Re = float(rng.uniform(60.0, 140.0))
+        U = cases.waveform_random(N, int(rng.integers(0, 2**31)), amp=0.4)
+        out.append((cases.pipe_case(N=N, Re=Re, Wo=5.0, amps=tuple(U), mesh=meshes[i % len(meshes)]), U, Re))
+    return out
+
+
+def _batched_ttr(ts, torch):
+    """Lockstep batched mixed solve vs the same instances one by one (mixed and plain FP64)."""
+    from workloads import meshgen as mg
+    meshes = [mg.pipe(nc=3, nr=2, nz=8), mg.pipe(nc=2, nr=2, nz=10), mg.pipe(nc=4, nr=3, nz=12),
+              mg.pipe(nc=3, nr=2, nz=16)]
+    inst = _pipe_family(np.random.default_rng(1000), 8, meshes)
+    opts = dict(tol=1e-8, max_steps=60, krylov=60, eps_ls=0.05, ser=1.0, raise_on_noconv=False)
+    res = {"workload": f"{len(inst)} pipe instances, {sorted(set(m.n_tets for m in meshes))} tets, "
+                       "N in {3,5,7}, Re U(60,140), Wo 5, own 1/n^2 waveforms"}
+    seq = {}
+    for prec, tau64 in ((32, "doublefloat"), (64, "refine")):
+        t, ok, fields = 0.0, True, []
+        for c, _, _ in inst:
+            g = ts.GLSProblem(c, variant="lin_a", dt_pseudo=0.5, tau64=tau64)
+            y = torch.tensor(c.y0, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rep = g.solve(y, precision=prec, **opts)
+            torch.cuda.synchronize()
+            t += time.perf_counter() - t0
+            ok = ok and rep["status"] == 0
+            fields.append(y)
+            g.close()
+        seq["mixed" if prec == 32 else "fp64"] = (t, ok, fields)
+    gs = [ts.GLSProblem(c, variant="lin_a", dt_pseudo=0.5) for c, _, _ in inst]
+    ys = [torch.tensor(c.y0, dtype=torch.float64, device="cuda") for c, _, _ in inst]
+    b = ts.Batch(gs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    reps = b.solve(ys, **opts)
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    res["batched_seconds"] = tb
+    res["batched_converged"] = all(r["status"] == 0 for r in reps)
+    res["launch_shape"] = b.launch_shape()
+    res["sequential_mixed_seconds"], res["sequential_mixed_converged"] = seq["mixed"][0], seq["mixed"][1]
+    res["sequential_fp64_seconds"], res["sequential_fp64_converged"] = seq["fp64"][0], seq["fp64"][1]
+    res["speedup_over_sequential_fp64"] = seq["fp64"][0] / tb
+    res["speedup_over_sequential_mixed"] = seq["mixed"][0] / tb
+    res["max_field_rel_l2_vs_sequential_fp64"] = max(
+        float((y - f).norm() / f.norm()) for y, f in zip(ys, seq["fp64"][2]))
+    b.close()
+    for g in gs:
+        g.close()
+    return res
+
+
+def _surrogate_ttr(ts, torch, n_train=32, n_test=4):
+    """Train the learned initial guess on solves of the method, then time held-out solves."""
+    from workloads import cases, meshgen as mg
+    mesh = mg.pipe(nc=3, nr=2, nz=10)
+    rng = np.random.default_rng(2000)
+    opts = dict(tol=1e-8, max_steps=60, krylov=60, eps_ls=0.05, ser=1.0, raise_on_noconv=False)
+
+    def sample():
+        Re = float(rng.uniform(60.0, 140.0))
+        U = cases.waveform_random(3, int(rng.integers(0, 2**31)), amp=0.4)
+        return cases.pipe_case(N=3, Re=Re, Wo=5.0, amps=tuple(U), mesh=mesh), U, Re
+
+    X, Y = [], []
+    t0 = time.perf_counter()
+    for _ in range(n_train):
+        c, U, Re = sample()
+        g = ts.GLSProblem(c, variant="lin_a", dt_pseudo=0.5)
+        y = torch.tensor(c.y0, dtype=torch.float64, device="cuda")
+        g.solve(y, precision=32, **opts)
+        X.append(cases.surrogate_inputs([U], Re, 5.0, harmonics=2))
+        Y.append(y.reshape(-1))
+        g.close()
+    Yd = torch.stack(Y)
+    s = ts.Surrogate(len(X[0]), 128, 3, 16, Yd.shape[1], seed=7)
+    s.fit_basis(Yd)
+    hist = s.train(np.array(X), Yd, epochs=400, batch=16, lr=2e-3, seed=8)
+    t_train = time.perf_counter() - t0
+    rows = []
+    for _ in range(n_test):
+        c, U, Re = sample()
+        x = cases.surrogate_inputs([U], Re, 5.0, harmonics=2)
+        row = {}
+        for name, prec, tau64, guess in (("fp64_plain", 64, "refine", False), ("mixed_plain", 32, "doublefloat", False),
+                                          ("mixed_surrogate", 32, "doublefloat", True)):
+            g = ts.GLSProblem(c, variant="lin_a", dt_pseudo=0.5, tau64=tau64)
+            y = torch.tensor(c.y0, dtype=torch.float64, device="cuda")
+            r_ref = float(g.residual(y).norm())
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            if guess:
+                s.guess(g, x, y)
+            rep = g.solve(y, precision=prec, r_ref=r_ref, **opts)
+            torch.cuda.synchronize()
+            row[name] = {"seconds": time.perf_counter() - t1, "steps": rep["steps"], "matvecs": rep["matvecs"],
+                         "converged": rep["status"] == 0}
+            g.close()
+        rows.append(row)
+    s.close()
+    agg = {k: {"seconds": sum(r[k]["seconds"] for r in rows), "steps": sum(r[k]["steps"] for r in rows),
+               "converged": all(r[k]["converged"] for r in rows)} for k in rows[0]}
+    return {"workload": f"pipe {mesh.n_tets} tets, N=3, Re U(60,140), Wo 5; {n_train} training solves, "
+                        f"{n_test} held out; network 6-128x3-16 (tanh), POD rank <= 16",
+            "train_seconds": t_train, "train_loss_first_last": [float(hist[0]), float(hist[-1])],
+            "held_out": agg,
+            "speedup_surrogate_over_fp64_plain": agg["fp64_plain"]["seconds"] / agg["mixed_surrogate"]["seconds"],
+            "speedup_surrogate_over_mixed_plain": agg["mixed_plain"]["seconds"] / agg["mixed_surrogate"]["seconds"]}
 
 
 def _oracle_step_rate(case, n_elem, n_jvp, seed=0):

@@ -93,7 +93,8 @@ typedef struct {
   int    precond;      /* 0: none; 1: right diagonal scaling by an approximate diag(H)
                           (viscous + mass + scalar-tau LS terms per node; changes the
                           GMRES path only, never the converged field)                  */
-  double ser;          /* > 0: pseudo-time step grows as dt_k = dt_0 (|r_0|/|r_k|)^ser
+  double ser;          /* > 0: pseudo-time step grows as dt_k = dt_0 (|r_0|/|r_k|)^ser,
+                          |r_0| = r_ref when given, else the first residual norm
                           (switched evolution relaxation; dt_0 = the problem's
                           dt_pseudo, which must be finite); 0: fixed dt (section 2.5.3) */
   double dt_max;       /* > 0: upper bound of the grown pseudo-time step (keeps the mass
@@ -204,6 +205,34 @@ int  ts_jvp(ts_problem* prob, const void* v, void* Hv, int precision, void* stre
  * the last iterate, report filled), TS_ERR_NAN on a non-finite norm. */
 int  ts_solve(ts_problem* prob, void* y_inout, const ts_solve_opts* opts,
               ts_solve_report* report, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched lockstep solve of many instances (no counterpart in the paper,
+ * which solves one problem at a time, section 2.5).  Instances may live on
+ * different meshes and use different N <= 7; each keeps its own boundary
+ * conditions, physics and pseudo-time schedule.  Every GMRES iteration
+ * applies the FP32 LIN_A tangent (eq. K_mat) of all instances in one fused
+ * launch and runs FP64 classical Gram-Schmidt as segmented reductions; the
+ * device work of an iteration is one CUDA graph per Krylov index.  The
+ * problems must outlive the batch; the batch works on its own stream and
+ * orders itself after / before the caller's stream.
+ * ------------------------------------------------------------------------- */
+typedef struct ts_batch ts_batch;
+/* TS_ERR_UNSUPPORTED if an instance has N > 7 (no single-launch kernel). */
+int  ts_batch_create(ts_problem* const* probs, int n, ts_batch** out);
+void ts_batch_free(ts_batch* batch);
+/* hv[b] = H_b v[b] (FP32, LIN_A, eq. K_mat + pseudo-time mass) for every
+ * instance, one fused launch plus the boundary terms; each instance needs a
+ * residual evaluation first (its linearisation state). */
+int  ts_batch_jvp(ts_batch* batch, const float* const* v, float* const* hv, void* stream);
+/* Mixed-precision pseudo-time Newton-GMRES (as ts_solve, precision 32) on
+ * every instance in lockstep; y[b] is instance b's FP64 field, reports[b]
+ * its report (seconds and times are of the whole batch).  TS_ERR_NOCONV if
+ * any instance hit the step cap (its report says which). */
+int  ts_batch_solve(ts_batch* batch, double* const* y, const ts_solve_opts* opts,
+                    ts_solve_report* reports, void* stream);
+/* launch shape chosen by the autotuner (1 once tuned, else 0) */
+int  ts_batch_launch_shape(const ts_batch* batch, int* warps_per_block, int* blocks);
 
 /* ---------------------------------------------------------------------------
  * Learned initial guess (no counterpart in the paper, whose Newton iteration

@@ -13,9 +13,9 @@ reference for the learned initial guess y0 = ybar + Phi diag(sigma) f(x):
   gradient of the loss (1 / 2B) sum_b ||f(x_b) - t_b||^2 by the chain rule,
   layer by layer in reverse.
 * ``adam_step``: Adam (Kingma & Ba 2015) with bias correction.
-* ``encode_inputs``: the network input for an inflow: real and imaginary
-  parts of harmonics 1..H of every inlet waveform, then (Re - 500) / 300 and
-  Wo / 10.
+
+The network inputs come from ``workloads.cases.surrogate_inputs`` (input
+encoding, shared with the GPU path).
 
 Row-major conventions shared with the CUDA kernels: a batch is X[B][n_in],
 a weight W_l[n_out][n_in] (out x in), so a layer is X W_l^T + b_l.
@@ -119,17 +119,3 @@ def adam_step(params, grads, state, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
         new.append(tuple(out))
     params[:] = new
     return params
-
-
-# ------------------------------------------------------------------ inputs
-
-def encode_inputs(waves, Re: float, Wo: float, harmonics: int = 4):
-    """waves: list of complex coefficient arrays (index n = mode), one per inlet."""
-    x = []
-    for U in waves:
-        U = np.asarray(U, dtype=np.complex128)
-        for n in range(1, harmonics + 1):
-            c = U[n] if n < U.size else 0.0
-            x += [np.real(c), np.imag(c)]
-    x += [(Re - 500.0) / 300.0, Wo / 10.0]
-    return np.asarray(x, dtype=np.float64)

@@ -105,6 +105,13 @@ def lib() -> ctypes.CDLL:
     L.ts_surrogate_train.argtypes = [vp, fp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                      u64, dp, vp]
     L.ts_surrogate_guess.argtypes = [vp, vp, fp, vp, vp]
+    L.ts_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp)]
+    L.ts_batch_free.argtypes = [vp]
+    L.ts_batch_free.restype = None
+    L.ts_batch_jvp.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
+    L.ts_batch_solve.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(ts_solve_opts),
+                                 ctypes.POINTER(ts_solve_report), vp]
+    L.ts_batch_launch_shape.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     L.ts_last_error.restype = ctypes.c_char_p
     L.ts_version.restype = ctypes.c_char_p
     L.ts_launch_count.restype = ctypes.c_int64
@@ -295,6 +302,80 @@ class GLSProblem:
         if getattr(self, "mesh", None):
             ts_mesh_free(self.mesh)
             self.mesh = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ batched solve
+
+def _ptr_array(ptrs):
+    return (ctypes.c_void_p * len(ptrs))(*[ctypes.c_void_p(int(p)) for p in ptrs])
+
+
+def ts_batch_create(probs):
+    h = ctypes.c_void_p()
+    arr = (ctypes.c_void_p * len(probs))(*[p.value if isinstance(p, ctypes.c_void_p) else p for p in probs])
+    _check(lib().ts_batch_create(arr, len(probs), ctypes.byref(h)))
+    return h
+
+
+def ts_batch_free(batch):
+    lib().ts_batch_free(batch)
+
+
+def ts_batch_jvp(batch, vs, hvs, stream=None):
+    _check(lib().ts_batch_jvp(batch, _ptr_array([v.data_ptr() for v in vs]),
+                              _ptr_array([h.data_ptr() for h in hvs]), _stream_ptr(stream)))
+    return hvs
+
+
+def ts_batch_solve(batch, ys, opts: ts_solve_opts, stream=None, raise_on_noconv=True):
+    reps = (ts_solve_report * len(ys))()
+    rc = lib().ts_batch_solve(batch, _ptr_array([y.data_ptr() for y in ys]), ctypes.byref(opts), reps,
+                              _stream_ptr(stream))
+    out = [r.to_dict() for r in reps]
+    for d in out:
+        d["status"] = rc
+    if rc != 0 and (raise_on_noconv or rc != TS_ERR_NOCONV):
+        raise TsError(rc, lib().ts_last_error().decode())
+    return out
+
+
+def ts_batch_launch_shape(batch):
+    w, b = ctypes.c_int(), ctypes.c_int()
+    tuned = lib().ts_batch_launch_shape(batch, ctypes.byref(w), ctypes.byref(b))
+    return {"warps_per_block": w.value, "blocks": b.value, "tuned": bool(tuned)}
+
+
+class Batch:
+    """Lockstep mixed-precision solve of several ``GLSProblem`` instances."""
+
+    def __init__(self, problems):
+        self.problems = list(problems)
+        self.h = ts_batch_create([p.prob for p in self.problems])
+
+    def jvp(self, vs, hvs=None, stream=None):
+        hvs = [p.field(v.dtype, v.device) for p, v in zip(self.problems, vs)] if hvs is None else hvs
+        return ts_batch_jvp(self.h, vs, hvs, stream)
+
+    def solve(self, ys, tol=1e-8, r_ref=0.0, max_steps=200, krylov=100, eps_ls=0.05, max_matvec=10000,
+              precond=1, ser=0.0, dt_max=0.0, stream=None, raise_on_noconv=True):
+        opts = ts_solve_opts(precision=32, tol=tol, r_ref=r_ref, max_steps=max_steps, krylov=krylov,
+                             eps_ls=eps_ls, max_matvec=max_matvec, verbose=0, precond=int(precond),
+                             ser=float(ser), dt_max=float(dt_max))
+        return ts_batch_solve(self.h, ys, opts, stream, raise_on_noconv)
+
+    def launch_shape(self):
+        return ts_batch_launch_shape(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            ts_batch_free(self.h)
+            self.h = None
 
     def __del__(self):
         try:

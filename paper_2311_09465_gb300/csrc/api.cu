@@ -100,6 +100,7 @@ struct ts_problem {
   double *d_w = nullptr, *d_r = nullptr, *d_dy = nullptr, *d_partial = nullptr, *d_h = nullptr;
   float *d_v32 = nullptr, *d_w32 = nullptr;
   double *d_D = nullptr, *d_t = nullptr;      // preconditioner diagonal (inverted), temp
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr; // time of the tangent products in a solve
   bool fast32 = true;    // FP32 products with the single-launch kernel (jvp32.cu)
   int tau64 = TS_TAU64_DOUBLEFLOAT;  // how the FP64 residual computes tau
 };
@@ -170,7 +171,8 @@ static int lin_alloc(ts_problem* pr, LinState<T>& l) {
     dft_tables(n, tn);
     std::copy(tn.begin(), tn.end(), all.begin() + dft_constant_offset(n));
   }
-  if (j32_upload_n123(all.data()) || j32_upload_n45(all.data()) || j32_upload_n7(all.data()))
+  if (j32_upload_n123(all.data()) || j32_upload_n45(all.data()) || j32_upload_n7(all.data()) ||
+      j32_upload_batch(all.data()))
     return fail(TS_ERR_CUDA, "DFT constant upload failed");
   return 0;
 }
@@ -422,7 +424,62 @@ static int jvp_any(ts_problem* pr, const void* v, void* hv, int precision, cudaS
 
 // ------------------------------------------------------------------ C ABI
 
+template <int N>
+static int j32_inst_impl(ts_problem* pr, J32Inst* I, cudaStream_t st) {
+  if constexpr (N > J32_MAX_N) {
+    return fail(TS_ERR_UNSUPPORTED, "batched tangent: no single-launch kernel for this N");
+  } else {
+    if (pr->p.jvp_variant != TS_JVP_LIN_A) return fail(TS_ERR_UNSUPPORTED, "batched tangent: LIN_A only");
+    TS_TRY(sync_dmask(pr));
+    LinState<float>& l = pr->l32;
+    if (!l.valid) {
+      if (!pr->l64.valid) return fail(TS_ERR_ARG, "batched tangent: no linearisation state");
+      TS_TRY(convert_lin<float, double, N>(pr, pr->l32, pr->l64, st));
+    }
+    const ts_mesh* m = pr->mesh;
+    *I = J32Inst{m->d_tets, m->d_geo32, nullptr, (const float*)l.u0t, (const float*)l.tau,
+                 (const float*)l.t0, pr->d_dmask, nullptr, phys_of<float>(pr, true), m->E, N};
+    return 0;
+  }
+}
+
+template <int N>
+static int j32_boundary_impl(ts_problem* pr, const float* v, float* hv, cudaStream_t st) {
+  for (auto& o : pr->outlets)
+    if (launch_outlet<float>(o.d_nodes, outlet_w<float>(o), (int)o.nodes.size(), (float)o.R, v,
+                             pr->d_dmask, 1, hv, pr->C, st))
+      return fail(TS_ERR_CUDA, "outlet kernel launch failed");
+  return backflow_terms<float, N>(pr, pr->l32, v, false, 1, hv, st);
+}
+
+static int precond_diag(ts_problem* pr, const double* y, double* D, cudaStream_t st) {
+  TS_TRY(sync_dmask(pr));
+  TS_CUDA(cudaMemsetAsync(D, 0, field_len(pr) * sizeof(double), st));
+  const ts_mesh* msh = pr->mesh;
+  Phys<double> ph = phys_of<double>(pr, true);
+  for (size_t c = 0; c + 1 < msh->colour_off.size(); ++c)
+    if (launch_diag(msh->d_tets, msh->d_geo64, y, pr->p.N, ph, D, msh->colour_off[c], msh->colour_off[c + 1], st))
+      return fail(TS_ERR_CUDA, "diag kernel");
+  if (launch_diag_invert(D, pr->d_dmask, msh->V, pr->C, st)) return fail(TS_ERR_CUDA, "diag invert");
+  return 0;
+}
+
 namespace ts {
+// operands of the problem's FP32 LIN_A tangent for the batched launch (v, out unset)
+int problem_j32_inst(ts_problem* pr, J32Inst* I, cudaStream_t st) {
+  TS_DISPATCH(pr->p.N, (j32_inst_impl<NN>(pr, I, st)));
+}
+// boundary terms of the FP32 tangent (resistance outlets, backflow), added to hv
+int problem_j32_boundary(ts_problem* pr, const float* v, float* hv, cudaStream_t st) {
+  TS_DISPATCH(pr->p.N, (j32_boundary_impl<NN>(pr, v, hv, st)));
+}
+// approximate inverse diagonal of the tangent at y (the right preconditioner of ts_solve)
+int problem_precond(ts_problem* pr, const double* y, double* D, cudaStream_t st) {
+  return precond_diag(pr, y, D, st);
+}
+int64_t problem_field_len(const ts_problem* pr) { return field_len(pr); }
+const ts_params* problem_params(const ts_problem* pr) { return &pr->p; }
+
 // the problem's Dirichlet mask on the device, storage coordinates per field, field length
 int problem_fixed_mask(ts_problem* pr, const uint8_t** dmask, int* C, int64_t* n) {
   TS_TRY(sync_dmask(pr));
@@ -619,7 +676,8 @@ int ts_problem_create(const ts_mesh* mesh, const ts_params* params, ts_problem**
   pr->dmask.assign(mesh->V, 0);
   {
   }
-  if (dalloc(&pr->d_dmask, (size_t)mesh->V) || dalloc(&pr->d_counter, 1)) {
+  if (dalloc(&pr->d_dmask, (size_t)mesh->V) || dalloc(&pr->d_counter, 1) ||
+      cudaEventCreate(&pr->ev_a) != cudaSuccess || cudaEventCreate(&pr->ev_b) != cudaSuccess) {
     ts_problem_free(pr);
     return TS_ERR_OOM;
   }
@@ -630,6 +688,8 @@ int ts_problem_create(const ts_mesh* mesh, const ts_params* params, ts_problem**
 
 void ts_problem_free(ts_problem* pr) {
   if (!pr) return;
+  if (pr->ev_a) cudaEventDestroy(pr->ev_a);
+  if (pr->ev_b) cudaEventDestroy(pr->ev_b);
   dfree(pr->d_dmask);
   dfree(pr->d_counter);
   for (auto& o : pr->outlets) {
@@ -925,7 +985,7 @@ int ts_solve(ts_problem* pr, void* y_inout, const ts_solve_opts* opts, ts_solve_
     TS_TRY(dalloc(&pr->d_r, n));
     TS_TRY(dalloc(&pr->d_dy, n));
     TS_TRY(dalloc(&pr->d_partial, (size_t)krylov_partial_blocks() * 128));
-    TS_TRY(dalloc(&pr->d_h, 128));
+    TS_TRY(dalloc(&pr->d_h, 3 * 130));
     TS_TRY(dalloc(&pr->d_v32, n));
     TS_TRY(dalloc(&pr->d_w32, n));
     TS_TRY(dalloc(&pr->d_D, n));
@@ -963,23 +1023,15 @@ int ts_solve(ts_problem* pr, void* y_inout, const ts_solve_opts* opts, ts_solve_
     }
     if (step == o.max_steps) break;
     if (ser) {
-      if (r_first < 0) r_first = rn;
+      // growth measured from the reference norm: a start closer to the root
+      // (a learned guess) begins with the step the plain start would have there
+      if (r_first < 0) r_first = o.r_ref > 0 ? o.r_ref : rn;
       double dt = dt0 * std::pow(r_first / rn, o.ser);
       if (o.dt_max > 0 && dt > o.dt_max) dt = o.dt_max;
       pr->p.dt_pseudo = dt > 1e8 * dt0 ? INFINITY : dt;
     }
     // right preconditioner: approximate inverse diagonal of the tangent
-    if (o.precond) {
-      TS_CUDA(cudaMemsetAsync(pr->d_D, 0, n * sizeof(double), st));
-      const ts_mesh* msh = pr->mesh;
-      Phys<double> ph = phys_of<double>(pr, true);
-      for (size_t c = 0; c + 1 < msh->colour_off.size(); ++c)
-        if (launch_diag(msh->d_tets, msh->d_geo64, y, pr->p.N, ph, pr->d_D, msh->colour_off[c],
-                        msh->colour_off[c + 1], st))
-          return fail(TS_ERR_CUDA, "diag kernel");
-      if (launch_diag_invert(pr->d_D, pr->d_dmask, msh->V, pr->C, st))
-        return fail(TS_ERR_CUDA, "diag invert");
-    }
+    if (o.precond) TS_TRY(precond_diag(pr, y, pr->d_D, st));
     // GMRES(m) on (H + c1 rho/dt M) D d' = -r, d = D d', from d = 0
     TS_CUDA(cudaMemsetAsync(pr->d_dy, 0, n * sizeof(double), st));
     double bnorm = rn;
@@ -994,7 +1046,8 @@ int ts_solve(ts_problem* pr, void* y_inout, const ts_solve_opts* opts, ts_solve_
       g[0] = beta;
       int k_used = 0;
       for (int k = 0; k < m; ++k) {
-        double tj = now_s();
+        const double tj = now_s();
+        TS_CUDA(cudaEventRecord(pr->ev_a, st));
         double* vk = V + (int64_t)k * n;
         if (o.precond) {
           if (vec_mul(pr->d_t, pr->d_D, vk, n, st)) return fail(TS_ERR_CUDA, "mul");
@@ -1007,28 +1060,32 @@ int ts_solve(ts_problem* pr, void* y_inout, const ts_solve_opts* opts, ts_solve_
         } else {
           TS_TRY(ts_jvp(pr, vk, pr->d_w, 64, st));
         }
-        TS_CUDA(cudaStreamSynchronize(st));
-        double tk = now_s();
-        rep->t_jvp += tk - tj;
+        TS_CUDA(cudaEventRecord(pr->ev_b, st));
         ++nmv;
-        // classical Gram-Schmidt, two passes
-        double hcol[130];
-        for (int j = 0; j <= k + 1; ++j) hcol[j] = 0;
+        // classical Gram-Schmidt, two passes, and the normalisation, all on the
+        // device: one host round trip per iteration returns the column
+        double* dh1 = pr->d_h;
+        double* dh2 = pr->d_h + 130;
+        double* dn2 = pr->d_h + 260;
         for (int pass = 0; pass < 2; ++pass) {
-          if (krylov_dots(V, n, k + 1, pr->d_w, n, pr->d_partial, pr->d_h, st))
-            return fail(TS_ERR_CUDA, "dots");
-          if (krylov_sub(pr->d_w, V, n, k + 1, pr->d_h, n, st)) return fail(TS_ERR_CUDA, "sub");
-          double hh[130];
-          TS_CUDA(cudaMemcpyAsync(hh, pr->d_h, (k + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
-          TS_CUDA(cudaStreamSynchronize(st));
-          for (int j = 0; j <= k; ++j) hcol[j] += hh[j];
+          double* dh = pass == 0 ? dh1 : dh2;
+          if (krylov_dots(V, n, k + 1, pr->d_w, n, pr->d_partial, dh, st)) return fail(TS_ERR_CUDA, "dots");
+          if (krylov_sub(pr->d_w, V, n, k + 1, dh, n, st)) return fail(TS_ERR_CUDA, "sub");
         }
-        double hn;
-        TS_TRY(dnorm(pr, pr->d_w, n, st, &hn));
+        if (krylov_dots(pr->d_w, n, 1, pr->d_w, n, pr->d_partial, dn2, st)) return fail(TS_ERR_CUDA, "norm");
+        if (vec_normalise(V + (int64_t)(k + 1) * n, pr->d_w, dn2, n, st)) return fail(TS_ERR_CUDA, "normalise");
+        double hh[3 * 130];
+        TS_CUDA(cudaMemcpyAsync(hh, pr->d_h, 3 * 130 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        TS_CUDA(cudaStreamSynchronize(st));
+        float ms_jvp = 0.f;
+        cudaEventElapsedTime(&ms_jvp, pr->ev_a, pr->ev_b);
+        rep->t_jvp += ms_jvp * 1e-3;
+        double tk = now_s();
+        rep->t_krylov += (tk - tj) - ms_jvp * 1e-3;
+        double hcol[130];
+        for (int j = 0; j <= k; ++j) hcol[j] = hh[j] + hh[130 + j];
+        const double hn = std::sqrt(std::max(hh[260], 0.0));
         hcol[k + 1] = hn;
-        if (hn > 0 && k + 1 < m + 1)
-          if (vec_scale(V + (int64_t)(k + 1) * n, pr->d_w, 1.0 / hn, n, st))
-            return fail(TS_ERR_CUDA, "scale");
         // Givens rotations on the new Hessenberg column
         for (int j = 0; j < k; ++j) {
           double t = cs[j] * hcol[j] + sn[j] * hcol[j + 1];

@@ -117,22 +117,6 @@ struct J32Layout {
   static constexpr int WARP = EPW * ELEM;
 };
 
-// One instance's operands of a tangent product (also the per-instance entry
-// of the batched launch).
-struct J32Inst {
-  const int4* tets;
-  const float* geo;
-  const float* v;
-  const float* u0t;
-  const float* tau;
-  const float* t0cache;
-  const uint8_t* dmask;
-  float* out;
-  Phys<float> ph;
-  int64_t n_elem;
-  int N;
-};
-
 // The EPW elements base, base + 1 of instance I on one warp; wsm is the
 // warp's shared-memory region (J32Layout<N, MODE>::WARP floats).
 template <int N, int MODE>
@@ -437,6 +421,44 @@ __global__ void __launch_bounds__(128) jvp32_kernel(J32Inst I) {
   for (int64_t base = ((int64_t)blockIdx.x * wpb + warp) * EPW; base < I.n_elem;
        base += (int64_t)gridDim.x * wpb * EPW)
     j32_pass<N, MODE>(I, base, smem + warp * L::WARP, lane);
+}
+
+__host__ __device__ constexpr bool j32_has(int N) { return dft_offset(N) >= 0; }
+
+// Tangent products of many instances in one launch.  Tile t (EPW elements)
+// belongs to the instance b with tile_off[b] <= t < tile_off[b + 1]; the
+// instance and tile counts are read from the device (counts[0], counts[1]) so
+// that a captured launch follows later changes of the tables; each warp
+// takes tiles grid-stride and runs the body compiled for that instance's N
+// (warp-uniform branch); shared memory is sized for the largest N.
+template <int MODE, int NMAX>
+__global__ void __launch_bounds__(128) jvp32_batch_kernel(const J32Inst* __restrict__ insts,
+                                                          const int64_t* __restrict__ tile_off,
+                                                          const int64_t* __restrict__ counts) {
+  extern __shared__ __align__(16) float smem[];
+  const int n_inst = (int)counts[0];
+  const int64_t n_tiles = counts[1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  float* wsm = smem + warp * J32Layout<NMAX, MODE>::WARP;
+  for (int64_t t = (int64_t)blockIdx.x * wpb + warp; t < n_tiles; t += (int64_t)gridDim.x * wpb) {
+    int lo = 0, hi = n_inst - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tile_off[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const J32Inst I = insts[lo];
+    const int64_t base = (t - tile_off[lo]) * EPW;
+    switch (I.N) {
+      case 1: if constexpr (j32_has(1)) j32_pass<1, MODE>(I, base, wsm, lane); break;
+      case 2: if constexpr (j32_has(2)) j32_pass<2, MODE>(I, base, wsm, lane); break;
+      case 3: if constexpr (j32_has(3)) j32_pass<3, MODE>(I, base, wsm, lane); break;
+      case 4: if constexpr (j32_has(4)) j32_pass<4, MODE>(I, base, wsm, lane); break;
+      case 5: if constexpr (j32_has(5)) j32_pass<5, MODE>(I, base, wsm, lane); break;
+      case 7: if constexpr (j32_has(7)) j32_pass<7, MODE>(I, base, wsm, lane); break;
+      default: break;
+    }
+  }
 }
 
 // u0 at the nodes sampled in time: u0t[V][3][K]

@@ -52,6 +52,32 @@ template <typename T>
 int launch_outlet(const int32_t* nodes, const T* w, int n_nodes, T R, const T* v,
                   const uint8_t* dmask, int mask_input, T* out, int C, cudaStream_t st);
 
+// One instance's operands of an FP32 tangent product (jvp32.cuh); also the
+// per-instance entry of the batched launch.
+struct J32Inst {
+  const int4* tets;
+  const float* geo;
+  const float* v;
+  const float* u0t;
+  const float* tau;
+  const float* t0cache;
+  const uint8_t* dmask;
+  float* out;
+  Phys<float> ph;
+  int64_t n_elem;
+  int N;
+};
+
+// Batched LIN_A tangent products of instances with N <= J32_MAX_N in one
+// launch (jvp32_batch.cu); every out must be zero on entry.  d_counts holds
+// {n_inst, n_tiles} on the device, tile_off n_inst + 1 prefix sums of
+// ceil(n_elem / 2).  Shared memory per warp: j32_batch_warp_bytes().
+int launch_jvp32_batch(const J32Inst* d_insts, const int64_t* d_tile_off, const int64_t* d_counts,
+                       int warps_per_block, int blocks, cudaStream_t st);
+size_t j32_batch_warp_bytes();
+int j32_batch_configure();
+int j32_upload_batch(const float* host_all);
+
 // FP32 tangent product, one launch (jvp32.cu); out must be zero on entry
 template <int N>
 int launch_jvp32(int mode, const int4* tets, const float* geo, const float* v, const float* u0t,
@@ -82,6 +108,8 @@ int vec_cast_d2f(float* out, const double* in, int64_t n, cudaStream_t st);
 int vec_cast_f2d(double* out, const float* in, int64_t n, cudaStream_t st);
 int krylov_partial_blocks();
 int vec_mul(double* out, const double* a, const double* b, int64_t n, cudaStream_t st);
+// out = in / sqrt(*n2) with the squared norm read on the device
+int vec_normalise(double* out, const double* in, const double* n2, int64_t n, cudaStream_t st);
 // approximate diagonal of the tangent for right preconditioning (one colour range)
 int launch_diag(const int4* tets, const double* geo, const double* y, int N, Phys<double> ph,
                 double* D, int64_t e0, int64_t e1, cudaStream_t st);

@@ -173,6 +173,21 @@ __global__ void mul_kernel(double* out, const double* a, const double* b, int64_
     out[i] = a[i] * b[i];
 }
 
+// out = in / sqrt(*n2) (zero when the norm vanishes); the norm stays on the device
+__global__ void scale_rsqrt_kernel(double* __restrict__ out, const double* __restrict__ in,
+                                   const double* __restrict__ n2, int64_t n) {
+  const double v = *n2;
+  const double s = v > 0 ? 1.0 / sqrt(v) : 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = in[i] * s;
+}
+
+int vec_normalise(double* out, const double* in, const double* n2, int64_t n, cudaStream_t st) {
+  count_launches(1);
+  scale_rsqrt_kernel<<<grid_for(n), 256, 0, st>>>(out, in, n2, n);
+  return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
 int vec_mul(double* out, const double* a, const double* b, int64_t n, cudaStream_t st) {
   count_launches(1);
   mul_kernel<<<grid_for(n), 256, 0, st>>>(out, a, b, n);

@@ -4,6 +4,7 @@ closed-form first Adam step, SVD identities."""
 import numpy as np
 
 from oracle import surrogate as sg
+from workloads import cases
 
 
 def _net(seed=0, sizes=(5, 7, 6, 3)):
@@ -99,7 +100,7 @@ def test_pod_basis_properties():
 def test_encode_inputs_layout():
     U1 = np.array([1.0, 0.1 + 0.2j, -0.3j, 0.05, 0.0, 0.0, 0.0])
     U2 = np.array([1.0, 0.4, 0.0, 0.0, -0.02j, 0.0, 0.0])
-    x = sg.encode_inputs([U1, U2], Re=800.0, Wo=10.0)
+    x = cases.surrogate_inputs([U1, U2], Re=800.0, Wo=10.0)
     assert x.shape == (18,)
     assert np.allclose(x[:8], [0.1, 0.2, 0.0, -0.3, 0.05, 0.0, 0.0, 0.0])
     assert np.allclose(x[8:16], [0.4, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, -0.02])

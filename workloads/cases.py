@@ -168,6 +168,23 @@ def junction_case(N: int = 7, Re: float = 500.0, Wo: float = 10.0, wave_seed: in
     return case
 
 
+# ------------------------------------------------------------------ learned-guess inputs
+
+def surrogate_inputs(waves, Re: float, Wo: float, harmonics: int = 4) -> np.ndarray:
+    """Network input for an inflow: Re and Im of harmonics 1..harmonics of every
+    inlet waveform (complex coefficients indexed by mode), then (Re - 500) / 300
+    and Wo / 10.  Two inlets with 4 harmonics give the 16 + 2 inputs of the
+    junction surrogate."""
+    x = []
+    for U in waves:
+        U = np.asarray(U, dtype=np.complex128)
+        for n in range(1, harmonics + 1):
+            c = U[n] if n < U.size else 0.0
+            x += [np.real(c), np.imag(c)]
+    x += [(Re - 500.0) / 300.0, Wo / 10.0]
+    return np.asarray(x, dtype=np.float64)
+
+
 # ------------------------------------------------------------------ random fields
 
 def random_state(mesh: mg.Mesh, N: int, seed: int, scale_u: float = 1.0, scale_p: float = 1.0,
