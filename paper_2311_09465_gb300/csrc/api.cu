@@ -55,7 +55,8 @@ struct LinState {
   T* tau = nullptr;     // [E][4][NT_PAD]
   T* t0 = nullptr;      // [E][4][3][C] tau L at the state
   T* dft = nullptr;     // forward [K][C] then inverse [C][K]
-  T* u0t = nullptr;     // [V][3][K] u0 velocity sampled in time (FP32 fast path)
+  T* u0t = nullptr;     // [V][K][4] u0 velocity sampled in time (FP32 fast path)
+  T* vt = nullptr;      // [V][K][4] scratch of the FP32 fast path: the product's input sampled
   T* bneg = nullptr;    // [backflow points][NT_PAD] |A_n|_- (section 2.6)
   int64_t bneg_points = 0;
   bool valid = false;
@@ -162,7 +163,10 @@ static int lin_alloc(ts_problem* pr, LinState<T>& l) {
   std::vector<T> tt(tab.begin(), tab.end());
   TS_TRY(dalloc(&l.dft, tt.size()));
   TS_CUDA(cudaMemcpy(l.dft, tt.data(), tt.size() * sizeof(T), cudaMemcpyHostToDevice));
-  TS_TRY(dalloc(&l.u0t, (size_t)m->V * 3 * pr->K));
+  if (sizeof(T) == 4) {
+    TS_TRY(dalloc(&l.u0t, (size_t)m->V * 4 * pr->K));
+    TS_TRY(dalloc(&l.vt, (size_t)m->V * 4 * pr->K));
+  }
   // constant-memory DFT tables of every compiled N (used by the FP32 fast path)
   std::vector<float> all(dft_constant_total());
   const int list[] = {TS_N_LIST};
@@ -184,6 +188,7 @@ static void lin_free(LinState<T>& l) {
   dfree(l.t0);
   dfree(l.dft);
   dfree(l.u0t);
+  dfree(l.vt);
   dfree(l.bneg);
   l.bneg_points = 0;
   l.valid = false;
@@ -376,12 +381,13 @@ static int jvp_impl(ts_problem* pr, const T* v, T* hv, cudaStream_t st) {
   }
   const int mode = mode_of_variant(pr->p.jvp_variant);
   if (mode < 0) return fail(TS_ERR_ARG, "unknown jvp variant");
-  TS_CUDA(cudaMemsetAsync(hv, 0, field_len(pr) * sizeof(T), st));
   if constexpr (sizeof(T) == 4 && N <= J32_MAX_N) if (pr->fast32) {
+    // the node pre-pass of the product clears hv
     const ts_mesh* m = pr->mesh;
-    int rc = launch_jvp32<N>(mode, m->d_tets, m->d_geo32, (const float*)v, (const float*)l.u0t,
-                             (const float*)l.tau, (const float*)l.t0, pr->d_dmask, (float*)hv,
-                             phys_of<float>(pr, true), m->E, st);
+    const J32Inst I{m->d_tets, m->d_geo32, (const float*)v, (const float*)l.u0t, (float*)l.vt,
+                    (const float*)l.tau, (const float*)l.t0, pr->d_dmask, (float*)hv,
+                    phys_of<float>(pr, true), m->E, m->V, N};
+    int rc = launch_jvp32<N>(mode, I, st);
     if (rc) return fail(TS_ERR_CUDA, "FP32 tangent kernel launch failed");
     for (auto& o : pr->outlets)
       if (launch_outlet<T>(o.d_nodes, outlet_w<T>(o), (int)o.nodes.size(), (T)o.R, v, pr->d_dmask, 1,
@@ -389,6 +395,7 @@ static int jvp_impl(ts_problem* pr, const T* v, T* hv, cudaStream_t st) {
         return fail(TS_ERR_CUDA, "outlet kernel launch failed");
     return backflow_terms<T, N>(pr, l, v, false, 1, hv, st);
   }
+  TS_CUDA(cudaMemsetAsync(hv, 0, field_len(pr) * sizeof(T), st));
   TS_TRY(apply_colours<T, N>(pr, mode, v, l.u0, l, hv, true, st));
   return backflow_terms<T, N>(pr, l, v, false, 1, hv, st);
 }
@@ -437,8 +444,8 @@ static int j32_inst_impl(ts_problem* pr, J32Inst* I, cudaStream_t st) {
       TS_TRY(convert_lin<float, double, N>(pr, pr->l32, pr->l64, st));
     }
     const ts_mesh* m = pr->mesh;
-    *I = J32Inst{m->d_tets, m->d_geo32, nullptr, (const float*)l.u0t, (const float*)l.tau,
-                 (const float*)l.t0, pr->d_dmask, nullptr, phys_of<float>(pr, true), m->E, N};
+    *I = J32Inst{m->d_tets, m->d_geo32, nullptr, (const float*)l.u0t, (float*)l.vt, (const float*)l.tau,
+                 (const float*)l.t0, pr->d_dmask, nullptr, phys_of<float>(pr, true), m->E, m->V, N};
     return 0;
   }
 }

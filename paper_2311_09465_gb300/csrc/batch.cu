@@ -209,7 +209,8 @@ struct ts_batch {
   std::vector<J32Inst> inst;          // per instance, v/out into the concatenated FP32 vectors
   J32Inst* d_inst = nullptr;
   int64_t* d_tile_off = nullptr;
-  int64_t* d_counts = nullptr;        // {instances, tiles} of the fused table
+  int64_t* d_node_off = nullptr;      // node prefix of the fused table (node pre-pass)
+  int64_t* d_counts = nullptr;        // {instances, tiles, nodes} of the fused table
   // chunk tables (all instances' chunks; the active ones first)
   int max_chunks = 0;
   int64_t *d_clo = nullptr, *d_chi = nullptr;
@@ -238,7 +239,7 @@ int set_active(ts_batch* B, const std::vector<char>& active, bool fused_tiles) {
   std::vector<int64_t> lo, hi;
   std::vector<int> ci, first(B->n, 0), nch(B->n, 0);
   std::vector<J32Inst> act;
-  std::vector<int64_t> toff(1, 0);
+  std::vector<int64_t> toff(1, 0), noff(1, 0);
   for (int b = 0; b < B->n; ++b) {
     if (!active[b]) continue;
     first[b] = (int)lo.size();
@@ -251,6 +252,7 @@ int set_active(ts_batch* B, const std::vector<char>& active, bool fused_tiles) {
     if (fused_tiles) {
       act.push_back(B->inst[b]);
       toff.push_back(toff.back() + (B->inst[b].n_elem + 1) / 2);
+      noff.push_back(noff.back() + B->inst[b].n_nodes);
     }
   }
   const int nc = (int)lo.size();
@@ -260,10 +262,12 @@ int set_active(ts_batch* B, const std::vector<char>& active, bool fused_tiles) {
   TS_CUDA(cudaMemcpyAsync(B->d_ccount, &nc, sizeof(int), cudaMemcpyHostToDevice, B->st));
   TS_CUDA(cudaMemcpyAsync(B->d_first, first.data(), B->n * sizeof(int), cudaMemcpyHostToDevice, B->st));
   TS_CUDA(cudaMemcpyAsync(B->d_nchunk, nch.data(), B->n * sizeof(int), cudaMemcpyHostToDevice, B->st));
-  int64_t counts[2] = {(int64_t)act.size(), toff.back()};
+  int64_t counts[3] = {(int64_t)act.size(), toff.back(), noff.back()};
   if (fused_tiles) {
     if (!act.empty()) {
       TS_CUDA(cudaMemcpyAsync(B->d_inst, act.data(), act.size() * sizeof(J32Inst), cudaMemcpyHostToDevice, B->st));
+      TS_CUDA(cudaMemcpyAsync(B->d_node_off, noff.data(), noff.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
+                              B->st));
       TS_CUDA(cudaMemcpyAsync(B->d_tile_off, toff.data(), toff.size() * sizeof(int64_t), cudaMemcpyHostToDevice,
                               B->st));
     }
@@ -278,7 +282,7 @@ int set_active(ts_batch* B, const std::vector<char>& active, bool fused_tiles) {
 
 // hv = J v for every instance in the fused table (v32 -> w32), boundary terms included
 int fused_tangent(ts_batch* B, const std::vector<char>& active) {
-  if (launch_jvp32_batch(B->d_inst, B->d_tile_off, B->d_counts, B->warps, B->blocks, B->st))
+  if (launch_jvp32_batch(B->d_inst, B->d_tile_off, B->d_node_off, B->d_counts, B->warps, B->blocks, B->st))
     return fail(TS_ERR_CUDA, "batched tangent launch failed");
   for (int b = 0; b < B->n; ++b)
     if (active[b])
@@ -484,7 +488,7 @@ int ts_batch_create(ts_problem* const* probs, int n, ts_batch** out) {
       !cuda_ok(cudaEventCreateWithFlags(&B->ev, cudaEventDisableTiming)) || j32_batch_configure())
     rc = fail(TS_ERR_CUDA, "ts_batch_create: stream set-up");
   if (!rc && ((rc = dalloc(&B->d_inst, n)) || (rc = dalloc(&B->d_tile_off, n + 1)) ||
-              (rc = dalloc(&B->d_counts, 2)) || (rc = dalloc(&B->d_clo, chunks)) ||
+              (rc = dalloc(&B->d_node_off, n + 1)) || (rc = dalloc(&B->d_counts, 3)) || (rc = dalloc(&B->d_clo, chunks)) ||
               (rc = dalloc(&B->d_chi, chunks)) || (rc = dalloc(&B->d_cinst, chunks)) ||
               (rc = dalloc(&B->d_ccount, 1)) || (rc = dalloc(&B->d_first, n)) || (rc = dalloc(&B->d_nchunk, n)) ||
               (rc = dalloc(&B->d_w, B->n_tot)) || (rc = dalloc(&B->d_r, B->n_tot)) ||
@@ -509,6 +513,7 @@ void ts_batch_free(ts_batch* B) {
   drop_graphs(B);
   dfree(B->d_inst);
   dfree(B->d_tile_off);
+  dfree(B->d_node_off);
   dfree(B->d_counts);
   dfree(B->d_clo);
   dfree(B->d_chi);

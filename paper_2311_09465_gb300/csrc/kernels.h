@@ -58,32 +58,34 @@ struct J32Inst {
   const int4* tets;
   const float* geo;
   const float* v;
-  const float* u0t;
+  const float* u0t;      // [V][K] float4: u0 velocity sampled in time (x, y, z, 0)
+  float* vt;             // [V][K] float4 scratch: masked v sampled in time (node pre-pass)
   const float* tau;
   const float* t0cache;
   const uint8_t* dmask;
   float* out;
   Phys<float> ph;
   int64_t n_elem;
+  int64_t n_nodes;
   int N;
 };
 
 // Batched LIN_A tangent products of instances with N <= J32_MAX_N in one
-// launch (jvp32_batch.cu); every out must be zero on entry.  d_counts holds
-// {n_inst, n_tiles} on the device, tile_off n_inst + 1 prefix sums of
-// ceil(n_elem / 2).  Shared memory per warp: j32_batch_warp_bytes().
-int launch_jvp32_batch(const J32Inst* d_insts, const int64_t* d_tile_off, const int64_t* d_counts,
-                       int warps_per_block, int blocks, cudaStream_t st);
+// element launch after one node pre-pass (jvp32_batch.cu); every out must be
+// zero on entry.  d_counts holds {n_inst, n_tiles, n_nodes} on the device,
+// tile_off n_inst + 1 prefix sums of ceil(n_elem / 2), node_off n_inst + 1
+// prefix sums of the node counts.  Shared memory per warp: j32_batch_warp_bytes().
+int launch_jvp32_batch(const J32Inst* d_insts, const int64_t* d_tile_off, const int64_t* d_node_off,
+                       const int64_t* d_counts, int warps_per_block, int blocks, cudaStream_t st);
 size_t j32_batch_warp_bytes();
 int j32_batch_configure();
 int j32_upload_batch(const float* host_all);
 
-// FP32 tangent product, one launch (jvp32.cu); out must be zero on entry
+// FP32 tangent product (jvp32.cuh): a node pre-pass (v sampled into I.vt,
+// I.out cleared) and one element launch
 template <int N>
-int launch_jvp32(int mode, const int4* tets, const float* geo, const float* v, const float* u0t,
-                 const float* tau, const float* t0, const uint8_t* dmask, float* out,
-                 Phys<float> ph, int64_t n_elem, cudaStream_t st);
-// u0 velocity at the nodes as time samples [V][3][K]
+int launch_jvp32(int mode, const J32Inst& I, cudaStream_t st);
+// u0 velocity at the nodes as time samples [V][K] float4 (x, y, z, 0)
 template <int N>
 int launch_node_samples(const float* u0, float* u0t, int64_t V, cudaStream_t st);
 // the table of all compiled N (forward [K][C] then inverse [C][K] each)
