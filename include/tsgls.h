@@ -99,6 +99,14 @@ typedef struct {
                           dt_pseudo, which must be finite); 0: fixed dt (section 2.5.3) */
   double dt_max;       /* > 0: upper bound of the grown pseudo-time step (keeps the mass
                           term in the tangent, so GMRES stays effective); 0: no bound */
+  double reject;       /* > 1 (ts_solve only, finite dt_pseudo): a step whose residual
+                          norm exceeds reject x the last accepted norm is undone and
+                          retried from the same state with a quarter of the pseudo-time
+                          step (at most 8 times in a row; the factor recovers x2 per
+                          accepted step); a step whose GMRES solve stalled above half
+                          its initial residual makes the next step 8x smaller.
+                          Changes the path only, never the converged field.
+                          <= 1: every step is accepted.  Not in the paper.           */
 } ts_solve_opts;
 
 typedef struct {
@@ -111,7 +119,8 @@ typedef struct {
   double t_jvp;         /* seconds in tangent products                          */
   double t_krylov;      /* seconds in Gram-Schmidt, norms and updates           */
   int    hist_len;      /* entries written to hist                              */
-  double hist[512];     /* ||r||/r_ref after each step                          */
+  double hist[512];     /* ||r||/r_ref after each step (rejected ones included) */
+  int    rejected;      /* steps undone by the reject test                      */
 } ts_solve_report;
 
 /* Copies a tetrahedral mesh to the device and precomputes per-element shape

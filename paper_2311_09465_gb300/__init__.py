@@ -45,7 +45,7 @@ class ts_solve_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("tol", ctypes.c_double), ("r_ref", ctypes.c_double),
                 ("max_steps", ctypes.c_int), ("krylov", ctypes.c_int), ("eps_ls", ctypes.c_double),
                 ("max_matvec", ctypes.c_int), ("verbose", ctypes.c_int), ("precond", ctypes.c_int),
-                ("ser", ctypes.c_double), ("dt_max", ctypes.c_double)]
+                ("ser", ctypes.c_double), ("dt_max", ctypes.c_double), ("reject", ctypes.c_double)]
 
 
 class ts_solve_report(ctypes.Structure):
@@ -53,7 +53,7 @@ class ts_solve_report(ctypes.Structure):
                 ("r_final", ctypes.c_double), ("seconds", ctypes.c_double),
                 ("t_residual", ctypes.c_double), ("t_jvp", ctypes.c_double),
                 ("t_krylov", ctypes.c_double), ("hist_len", ctypes.c_int),
-                ("hist", ctypes.c_double * 512)]
+                ("hist", ctypes.c_double * 512), ("rejected", ctypes.c_int)]
 
     def to_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "hist"}
@@ -288,11 +288,11 @@ class GLSProblem:
 
     def solve(self, y, precision=64, tol=1e-8, r_ref=0.0, max_steps=200, krylov=100,
               eps_ls=0.05, max_matvec=10000, verbose=False, stream=None, raise_on_noconv=True,
-              precond=1, ser=0.0, dt_max=0.0):
+              precond=1, ser=0.0, dt_max=0.0, reject=4.0):
         opts = ts_solve_opts(precision=precision, tol=tol, r_ref=r_ref, max_steps=max_steps,
                              krylov=krylov, eps_ls=eps_ls, max_matvec=max_matvec,
                              verbose=int(verbose), precond=int(precond), ser=float(ser),
-                             dt_max=float(dt_max))
+                             dt_max=float(dt_max), reject=float(reject))
         return ts_solve(self.prob, y, opts, stream=stream, raise_on_noconv=raise_on_noconv)
 
     def close(self):

@@ -1009,6 +1009,12 @@ int ts_solve(ts_problem* pr, void* y_inout, const ts_solve_opts* opts, ts_solve_
   const double dt0 = pr->p.dt_pseudo;
   const bool ser = o.ser > 0 && dt0 > 0 && std::isfinite(dt0);
   double r_first = -1;
+  // step rejection: the last accepted norm, the pseudo-time step factor, and
+  // whether the coming residual is the re-evaluation at a restored state
+  const bool rejecting = o.reject > 1 && dt0 > 0 && std::isfinite(dt0);
+  double rel_acc = -1, backoff = 1.0;
+  int n_rej = 0;
+  bool retry = false;
   for (step = 0; step <= o.max_steps; ++step) {
     double t0 = now_s();
     TS_TRY(ts_residual(pr, y, pr->d_r, 64, st));
@@ -1029,13 +1035,32 @@ int ts_solve(ts_problem* pr, void* y_inout, const ts_solve_opts* opts, ts_solve_
       break;
     }
     if (step == o.max_steps) break;
+    if (rejecting && !retry && rel_acc > 0 && rel > o.reject * rel_acc && n_rej < 8) {
+      // undo the last update; the next pass re-evaluates the residual there
+      // and retries with a smaller pseudo-time step
+      if (vec_axpy(y, pr->d_dy, -1.0, n, st)) return fail(TS_ERR_CUDA, "axpy");
+      backoff *= 0.25;
+      ++n_rej;
+      ++rep->rejected;
+      retry = true;
+      continue;
+    }
+    if (!retry) {
+      n_rej = 0;
+      if (rel_acc > 0) backoff = std::min(1.0, 2.0 * backoff);
+    }
+    retry = false;
+    rel_acc = rel;
     if (ser) {
       // growth measured from the reference norm: a start closer to the root
       // (a learned guess) begins with the step the plain start would have there
       if (r_first < 0) r_first = o.r_ref > 0 ? o.r_ref : rn;
       double dt = dt0 * std::pow(r_first / rn, o.ser);
       if (o.dt_max > 0 && dt > o.dt_max) dt = o.dt_max;
+      dt *= backoff;
       pr->p.dt_pseudo = dt > 1e8 * dt0 ? INFINITY : dt;
+    } else if (rejecting) {
+      pr->p.dt_pseudo = dt0 * backoff;
     }
     // right preconditioner: approximate inverse diagonal of the tangent
     if (o.precond) TS_TRY(precond_diag(pr, y, pr->d_D, st));
@@ -1046,6 +1071,7 @@ int ts_solve(ts_problem* pr, void* y_inout, const ts_solve_opts* opts, ts_solve_
     TS_CUDA(cudaMemcpyAsync(pr->d_w, pr->d_r, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     int nmv = 0;
     bool done = false;
+    double lin_res = bnorm;   // last estimate of the linear residual
     while (!done && nmv < o.max_matvec) {
       // V0 = -(current linear residual) / beta ; the residual lives in d_w
       if (vec_scale(V, pr->d_w, -1.0 / beta, n, st)) return fail(TS_ERR_CUDA, "scale");
@@ -1123,6 +1149,7 @@ int ts_solve(ts_problem* pr, void* y_inout, const ts_solve_opts* opts, ts_solve_
       if (vec_axpy(pr->d_dy, pr->d_w, 1.0, n, st)) return fail(TS_ERR_CUDA, "axpy");
       rep->t_krylov += now_s() - tk;
       double est = std::fabs(g[k_used]);
+      lin_res = est;
       if (est <= o.eps_ls * bnorm || nmv >= o.max_matvec) {
         done = true;
       } else {
@@ -1140,10 +1167,14 @@ int ts_solve(ts_problem* pr, void* y_inout, const ts_solve_opts* opts, ts_solve_
         // d_w = J d + r  (= -(b - J d)), the scale at the loop head negates it
         if (vec_axpy(pr->d_w, pr->d_r, 1.0, n, st)) return fail(TS_ERR_CUDA, "axpy");
         TS_TRY(dnorm(pr, pr->d_w, n, st, &beta));
+        lin_res = beta;
         if (beta <= o.eps_ls * bnorm) done = true;
       }
     }
     rep->matvecs += nmv;
+    // a linear solve that stalled (restarted GMRES can stagnate once the mass
+    // term has faded): shrink the next pseudo-time step
+    if (rejecting && lin_res > 0.5 * bnorm) backoff *= 0.125;
     if (vec_axpy(y, pr->d_dy, 1.0, n, st)) return fail(TS_ERR_CUDA, "axpy");
   }
   pr->p.dt_pseudo = dt0;

@@ -395,30 +395,30 @@ int launch_apply(int mode, const int4* tets, const T* geo, const T* v, const T* 
 }
 
 // ---------------------------------------------------------------- outlets
-// One block per call: Q_c = sum_A sum_i w_Ai v[A][i][c]; out[A][i][c] += R w_Ai Q_c
+// One block per call: Q_c = sum_A sum_i w_Ai v[A][i][c]; out[A][i][c] += R w_Ai Q_c.
+// Warp w reduces the flow rates Q_c of the coefficients c = w, w + 16, ...
+// over the outlet nodes (shuffle reduction), then all threads scatter.
 template <typename T>
-__global__ void outlet_kernel(const int32_t* __restrict__ nodes, const T* __restrict__ w, int n,
-                              T R, const T* __restrict__ v, const uint8_t* __restrict__ dmask,
-                              int mask_input, T* __restrict__ out, int C) {
-  __shared__ T part[256];
+__global__ void __launch_bounds__(512) outlet_kernel(const int32_t* __restrict__ nodes,
+                                                     const T* __restrict__ w, int n, T R,
+                                                     const T* __restrict__ v,
+                                                     const uint8_t* __restrict__ dmask, int mask_input,
+                                                     T* __restrict__ out, int C) {
   __shared__ T Q[128];
-  for (int c = 0; c < C; ++c) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int c = warp; c < C; c += nw) {
     T acc = 0;
-    for (int b = threadIdx.x; b < n; b += blockDim.x) {
+    for (int b = lane; b < n; b += 32) {
       const int A = nodes[b];
       if (mask_input && dmask[A]) continue;
       const T* va = v + (int64_t)A * 4 * C;
       acc += w[b * 3 + 0] * va[0 * C + c] + w[b * 3 + 1] * va[1 * C + c] + w[b * 3 + 2] * va[2 * C + c];
     }
-    part[threadIdx.x] = acc;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-      if (threadIdx.x < s) part[threadIdx.x] += part[threadIdx.x + s];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) Q[c] = (c == 1) ? T(0) : part[0];
-    __syncthreads();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) Q[c] = (c == 1) ? T(0) : acc;
   }
+  __syncthreads();
   for (int t = threadIdx.x; t < n * 3 * C; t += blockDim.x) {
     const int b = t / (3 * C), r = t - b * 3 * C;
     const int i = r / C, c = r - i * C;
@@ -434,7 +434,7 @@ int launch_outlet(const int32_t* nodes, const T* w, int n_nodes, T R, const T* v
   if (n_nodes <= 0) return 0;
   if (C > 128) return -1;
   count_launches(1);
-  outlet_kernel<T><<<1, 256, 0, st>>>(nodes, w, n_nodes, R, v, dmask, mask_input, out, C);
+  outlet_kernel<T><<<1, 512, 0, st>>>(nodes, w, n_nodes, R, v, dmask, mask_input, out, C);
   return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 

@@ -38,6 +38,49 @@ namespace {
 
 __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
 
+// shared-memory rows: M floats from a 16-byte aligned row padded to a multiple
+// of 4 (ld4/st4: 16-byte accesses, st4 writes zeros into the padding), or an
+// even count from an 8-byte aligned row (ld2)
+template <int M>
+__device__ __forceinline__ void ld4(const float* p, float (&x)[M]) {
+  const float4* p4 = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int c4 = 0; c4 < (M + 3) / 4; ++c4) {
+    const float4 v = p4[c4];
+    const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (4 * c4 + u < M) x[4 * c4 + u] = e[u];
+  }
+}
+template <int M>
+__device__ __forceinline__ void st4(float* p, const float (&x)[M]) {
+  float4* p4 = reinterpret_cast<float4*>(p);
+#pragma unroll
+  for (int c4 = 0; c4 < (M + 3) / 4; ++c4) {
+    float e[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) e[u] = 4 * c4 + u < M ? x[4 * c4 + u] : 0.f;
+    p4[c4] = make_float4(e[0], e[1], e[2], e[3]);
+  }
+}
+template <int M>
+__device__ __forceinline__ void ld2(const float* p, float (&x)[M]) {
+  const float2* p2 = reinterpret_cast<const float2*>(p);
+#pragma unroll
+  for (int c2 = 0; c2 < M / 2; ++c2) {
+    const float2 v = p2[c2];
+    x[2 * c2] = v.x;
+    x[2 * c2 + 1] = v.y;
+  }
+}
+template <int M>
+__device__ __forceinline__ void st2(float* p, const float (&x)[M]) {
+  float2* p2 = reinterpret_cast<float2*>(p);
+#pragma unroll
+  for (int c2 = 0; c2 < M / 2; ++c2) p2[c2] = make_float2(x[2 * c2], x[2 * c2 + 1]);
+}
+
 // ---------------------------------------------------------------- DFT tables
 // forward [K][C] then inverse [C][K] for each N of this unit, concatenated:
 // forward (k, 2n) = 2 cos(2 pi n k / K), (k, 2n+1) = -2 sin(2 pi n k / K),
@@ -212,6 +255,7 @@ constexpr unsigned FULL = 0xffffffffu;
 template <int N, int MODE>
 struct J32Layout {
   static constexpr int C = 2 * N, K = 3 * N - 2, NTP = Dims<N>::NT_PAD;
+  static constexpr int KP = (K + 3) & ~3;   // sample rows padded to 16 bytes
   static constexpr bool LINA = MODE == MODE_JVP_LIN_A;
   static constexpr int STG_TAU = 0;                               // [2][4][NTP]
   static constexpr int STG_T0 = STG_TAU + EPW * 4 * NTP;          // [2][4][3][C] (LIN_A)
@@ -221,10 +265,14 @@ struct J32Layout {
   static constexpr int GM = VM + 16 * C;               // gradients [4 f][3 j][C]
   static constexpr int VS = GM + 12 * C;               // sum over nodes [4 f][C]
   static constexpr int GE = VS + 4 * C;                // dN_a/dx_j [12], volume, pad, node ids [4]
-  static constexpr int CT = GE + 20;                   // c, later T samples [4 q][3 i][K]
-  static constexpr int TS = CT + 12 * K;               // T0 samples [4 q][3 i][K] (LIN_A)
-  static constexpr int WS = TS + (LINA ? 12 * K : 0);  // SUPG sums [3 j][3 i][K], then modes
-  static constexpr int ELEM = (WS + 9 * K + 3) & ~3;
+  static constexpr int CT = GE + 20;                    // c, later T samples [4 q][3 i][KP]
+  static constexpr int TS = CT + 12 * KP;               // T0 samples [4 q][3 i][KP] (LIN_A)
+  // SUPG sums [3 j][3 i][KP], then Z modes; they take the place of v at the nodes
+  // (dead after the point phase) when that is large enough
+  static constexpr bool WS_IN_VM = 9 * KP <= 16 * C;
+  static constexpr int END = TS + (LINA ? 12 * KP : 0);
+  static constexpr int WS = WS_IN_VM ? VM : END;
+  static constexpr int ELEM = WS_IN_VM ? END : END + 9 * KP;
   static constexpr int WORK = EPW * ELEM;
   static constexpr int WARP = STG + WORK;
 };
@@ -298,19 +346,22 @@ __device__ __forceinline__ bool j32_pass(const J32Inst I, int64_t base, const fl
   // ---- P1: lane (f, j < 3) the gradient of field f; lane (f, 3) the sum over the nodes
   {
     const float* vm = es + L::VM;
+    float d[4] = {1.f, 1.f, 1.f, 1.f};   // lane (f, 3): plain sum over the nodes
     if (q < 3) {
-      const float d0 = es[L::GE + 0 * 3 + q], d1 = es[L::GE + 1 * 3 + q];
-      const float d2 = es[L::GE + 2 * 3 + q], d3 = es[L::GE + 3 * 3 + q];
 #pragma unroll
-      for (int c = 0; c < C; ++c)
-        es[L::GM + (f * 3 + q) * C + c] = d0 * vm[(0 * 4 + f) * C + c] + d1 * vm[(1 * 4 + f) * C + c] +
-                                          d2 * vm[(2 * 4 + f) * C + c] + d3 * vm[(3 * 4 + f) * C + c];
-    } else {
-#pragma unroll
-      for (int c = 0; c < C; ++c)
-        es[L::VS + f * C + c] = vm[(0 * 4 + f) * C + c] + vm[(1 * 4 + f) * C + c] + vm[(2 * 4 + f) * C + c] +
-                                vm[(3 * 4 + f) * C + c];
+      for (int a = 0; a < 4; ++a) d[a] = es[L::GE + a * 3 + q];
     }
+    float acc[C], x[C];
+    ld2<C>(vm + (0 * 4 + f) * C, x);
+#pragma unroll
+    for (int c = 0; c < C; ++c) acc[c] = d[0] * x[c];
+#pragma unroll
+    for (int a = 1; a < 4; ++a) {
+      ld2<C>(vm + (a * 4 + f) * C, x);
+#pragma unroll
+      for (int c = 0; c < C; ++c) acc[c] = fmaf(d[a], x[c], acc[c]);
+    }
+    st2<C>(es + (q < 3 ? L::GM + (f * 3 + q) * C : L::VS + f * C), acc);
   }
   // ---- A: one lane per (element, sample): convective products c_i(q, t_k)
   const float4* __restrict__ u0t = reinterpret_cast<const float4*>(I.u0t);
@@ -321,8 +372,7 @@ __device__ __forceinline__ bool j32_pass(const J32Inst I, int64_t base, const fl
     const float* g = work + s * L::ELEM + L::GE;
     const int4 nd = *reinterpret_cast<const int4*>(g + 16);
     float dN[12];
-#pragma unroll
-    for (int j = 0; j < 12; ++j) dN[j] = g[j];
+    ld4<12>(g, dN);
     const int na[4] = {nd.x, nd.y, nd.z, nd.w};
     float ua[4][3], va[4][3];
 #pragma unroll
@@ -362,7 +412,7 @@ __device__ __forceinline__ bool j32_pass(const J32Inst I, int64_t base, const fl
           acc = fmaf(fmaf(QD, ua[qq][j], su[j]), gv[i][j], acc);
           if (LINA) acc = fmaf(fmaf(QD, va[qq][j], sv[j]), gu[i][j], acc);
         }
-        ct[(qq * 3 + i) * K] = acc;
+        ct[(qq * 3 + i) * L::KP] = acc;
       }
   }
   __syncwarp();
@@ -370,10 +420,12 @@ __device__ __forceinline__ bool j32_pass(const J32Inst I, int64_t base, const fl
   float rowp[C];   // node-row part known after this phase (lane (f, a = q))
   float sT[C];
   float X[C];
+  float extra[C];  // velocity row a = q: consistent mass and pressure terms
 #pragma unroll
   for (int c = 0; c < C; ++c) {
     X[c] = 0.f;
     sT[c] = 0.f;
+    extra[c] = 0.f;
   }
   if (!__all_sync(FULL, mbar_wait(bar, parity))) return false;   // nothing added yet
   if (f < 3) {
@@ -381,19 +433,17 @@ __device__ __forceinline__ bool j32_pass(const J32Inst I, int64_t base, const fl
     float cm[C];
     {
       float ctv[K];
-      const float* src = es + L::CT + (q * 3 + i) * K;
-#pragma unroll
-      for (int k = 0; k < K; ++k) ctv[k] = src[k];
+      ld4<K>(es + L::CT + (q * 3 + i) * L::KP, ctv);
       inv<N>(ctv, cm);
     }
     float G[C], Lm[C], dp[C];
     {
-      float vq[C];
+      float vq[C], vs[C];
+      ld2<C>(es + L::VM + (q * 4 + i) * C, vq);
+      ld2<C>(es + L::VS + i * C, vs);
+      ld2<C>(es + L::GM + (3 * 3 + i) * C, dp);
 #pragma unroll
-      for (int c = 0; c < C; ++c) {
-        vq[c] = fmaf(QD, es[L::VM + (q * 4 + i) * C + c], QB * es[L::VS + i * C + c]);
-        dp[c] = es[L::GM + (3 * 3 + i) * C + c];
-      }
+      for (int c = 0; c < C; ++c) vq[c] = fmaf(QD, vq[c], QB * vs[c]);
 #pragma unroll
       for (int c = 0; c < C; ++c) {
         G[c] = (c == 1) ? 0.f : rho * (om_apply<N>(vq, c, omega) + cm[c]);
@@ -417,19 +467,24 @@ __device__ __forceinline__ bool j32_pass(const J32Inst I, int64_t base, const fl
     {
       float Tt[K];
       fwd<N>(T, Tt);
-      float* dst = es + L::CT + (q * 3 + i) * K;
-#pragma unroll
-      for (int k = 0; k < K; ++k) dst[k] = Tt[k];
+      st4<K>(es + L::CT + (q * 3 + i) * L::KP, Tt);
     }
     if (LINA) {
       float T0m[C], T0t[K];
-      const float* src = stg + L::STG_T0 + ((slot * 4 + q) * 3 + i) * C;
-#pragma unroll
-      for (int c = 0; c < C; ++c) T0m[c] = src[c];
+      ld2<C>(stg + L::STG_T0 + ((slot * 4 + q) * 3 + i) * C, T0m);
       fwd<N>(T0m, T0t);
-      float* dst = es + L::TS + (q * 3 + i) * K;
+      st4<K>(es + L::TS + (q * 3 + i) * L::KP, T0t);
+    }
+    {
+      // row (a = q, i): mass_coef V/20 (sum_b v_ib + v_ia) - dN_a/dx_i V pbar
+      float vs[C], vm[C], ps[C];
+      ld2<C>(es + L::VS + i * C, vs);
+      ld2<C>(es + L::VM + (q * 4 + i) * C, vm);
+      ld2<C>(es + L::VS + 3 * C, ps);
+      const float vol = es[L::GE + GEO_VOL];
+      const float mc = I.ph.mass_coef * vol * 0.05f, pv = 0.25f * es[L::GE + q * 3 + i] * vol;
 #pragma unroll
-      for (int k = 0; k < K; ++k) dst[k] = T0t[k];
+      for (int c = 0; c < C; ++c) extra[c] = fmaf(mc, vs[c] + vm[c], -pv * ps[c]);
     }
   }
   __syncwarp();
@@ -441,7 +496,7 @@ __device__ __forceinline__ bool j32_pass(const J32Inst I, int64_t base, const fl
     float x = X[c];
     x += __shfl_xor_sync(FULL, x, 1);
     x += __shfl_xor_sync(FULL, x, 2);
-    rowp[c] = w4 * fmaf(QD, X[c], QB * x);   // Galerkin + (-Omega N_a) LS, velocity lanes
+    rowp[c] = fmaf(w4, fmaf(QD, X[c], QB * x), extra[c]);   // Galerkin + (-Omega N_a) LS, velocity lanes
     float y = sT[c];
     y += __shfl_xor_sync(FULL, y, 1);
     y += __shfl_xor_sync(FULL, y, 2);
@@ -501,8 +556,8 @@ __device__ __forceinline__ bool j32_pass(const J32Inst I, int64_t base, const fl
       }
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
-        const float Ti = ew[L::CT + (qq * 3 + i) * K + k];
-        const float T0i = LINA ? ew[L::TS + (qq * 3 + i) * K + k] : 0.f;
+        const float Ti = ew[L::CT + (qq * 3 + i) * L::KP + k];
+        const float T0i = LINA ? ew[L::TS + (qq * 3 + i) * L::KP + k] : 0.f;
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
           W[j][i] = fmaf(uq[j], Ti, W[j][i]);
@@ -514,19 +569,24 @@ __device__ __forceinline__ bool j32_pass(const J32Inst I, int64_t base, const fl
 #pragma unroll
     for (int j = 0; j < 3; ++j)
 #pragma unroll
-      for (int i = 0; i < 3; ++i) ws[(j * 3 + i) * K] = W[j][i];
+      for (int i = 0; i < 3; ++i) ws[(j * 3 + i) * L::KP] = W[j][i];
   }
   __syncwarp();
-  // ---- D: SUPG sums to modes, one lane per (element, j, i); in place
+  // ---- D: SUPG sums to modes, one lane per (element, j, i), in place, with the
+  // viscous gradient folded in: Z_ji = w W_ji + mu V dv_i/dx_j
   if (lane < EPW * 9) {
     const int s = lane >= 9 ? 1 : 0, ji = lane - 9 * s;
-    float* p = work + s * L::ELEM + L::WS + ji * K;
-    float wt[K], wm[C];
-#pragma unroll
-    for (int k = 0; k < K; ++k) wt[k] = p[k];
+    const int j = ji / 3, i = ji - 3 * j;
+    const float* ew = work + s * L::ELEM;
+    float* p = work + s * L::ELEM + L::WS + ji * L::KP;
+    float wt[K], wm[C], gm[C];
+    ld4<K>(p, wt);
     inv<N>(wt, wm);
+    ld2<C>(ew + L::GM + (i * 3 + j) * C, gm);
+    const float vol_s = ew[L::GE + GEO_VOL], w4_s = 0.25f * vol_s, mv = I.ph.mu * vol_s;
 #pragma unroll
-    for (int c = 0; c < C; ++c) p[c] = wm[c];
+    for (int c = 0; c < C; ++c) wm[c] = fmaf(w4_s, wm[c], mv * gm[c]);
+    st2<C>(p, wm);
   }
   __syncwarp();
   // ---- E: node rows, lane (f, a = q)
@@ -534,34 +594,28 @@ __device__ __forceinline__ bool j32_pass(const J32Inst I, int64_t base, const fl
     const int a = q;
     const int4 nd = *reinterpret_cast<const int4*>(es + L::GE + 16);
     const int node = a == 0 ? nd.x : a == 1 ? nd.y : a == 2 ? nd.z : nd.w;
-    const float vol = es[L::GE + GEO_VOL];
     const float da[3] = {es[L::GE + a * 3 + 0], es[L::GE + a * 3 + 1], es[L::GE + a * 3 + 2]};
     const bool fixed = live ? I.dmask[node] != 0 : true;
-    float row[C];
+    float row[C], x[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) row[c] = rowp[c];
     if (f < 3) {
       const int i = f;
-      const float dai = i == 0 ? da[0] : i == 1 ? da[1] : da[2];
-      const float mv = I.ph.mu * vol, pv = 0.25f * dai * vol, mc = I.ph.mass_coef * vol * 0.05f;
 #pragma unroll
-      for (int c = 0; c < C; ++c) {
-        float supg = 0.f, visc = 0.f;
+      for (int j = 0; j < 3; ++j) {   // SUPG + viscous
+        ld2<C>(es + L::WS + (j * 3 + i) * L::KP, x);
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          supg = fmaf(da[j], es[L::WS + (j * 3 + i) * K + c], supg);
-          visc = fmaf(da[j], es[L::GM + (i * 3 + j) * C + c], visc);
-        }
-        float m = rowp[c] + w4 * supg + mv * visc - pv * es[L::VS + 3 * C + c];
-        m = fmaf(mc, es[L::VS + i * C + c] + es[L::VM + (a * 4 + i) * C + c], m);
-        row[c] = (c == 1) ? 0.f : m;
+        for (int c = 0; c < C; ++c) row[c] = fmaf(da[j], x[c], row[c]);
       }
     } else {
 #pragma unroll
-      for (int c = 0; c < C; ++c) {
-        const float div = es[L::GM + (0 * 3 + 0) * C + c] + es[L::GM + (1 * 3 + 1) * C + c] +
-                          es[L::GM + (2 * 3 + 2) * C + c];
-        row[c] = (c == 1) ? 0.f : fmaf(w4, div, rowp[c]);
+      for (int d = 0; d < 3; ++d) {   // w div v
+        ld2<C>(es + L::GM + (d * 3 + d) * C, x);
+#pragma unroll
+        for (int c = 0; c < C; ++c) row[c] = fmaf(w4, x[c], row[c]);
       }
     }
+    row[1] = 0.f;
     if (live && !(f < 3 && fixed)) row_atomics<C>(I.out + ((int64_t)node * 4 + f) * C, row);
   }
   __syncwarp();
