@@ -45,6 +45,14 @@ SOLVE_OPTS = dict(tol=1e-8, krylov=100, eps_ls=0.05, max_matvec=1000, precond=1,
                   raise_on_noconv=False)
 
 
+def _sm_max_mhz():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["sm_max_mhz"])
+    except Exception:
+        return 2070.0
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -136,14 +144,29 @@ def _jvp_bytes(case, b=4):
             + E * 4 * 3 * 2 * N * b)           # tau L(u0) per point (LIN_A)
 
 
-def _profile_traffic(kernel_src):
-    """DRAM traffic per tangent product from the committed ncu summary, if still current."""
+def _tau_dd_instr(case):
+    """FP32 instructions of the double-float refinement in one tau_dd launch.
+
+    Per quadrature point (n = 2N - 1, t = n(n+1)/2): M (3 t n), the second
+    Newton-Schulz Gram matrix, B and tau (t n each, symmetric) and the four
+    full products V H twice, M V, Z V^T (n^3 each) are double-float
+    multiply-adds of 15 FP32 instructions; the first Gram matrix (t n) takes
+    FP32 factors, 13 instructions.  The FP32 Jacobi sweeps (data-dependent
+    count) are not counted."""
+    n = 2 * case.N - 1
+    t = n * (n + 1) // 2
+    per_point = 15 * (6 * t * n + 4 * n ** 3) + 13 * t * n
+    return 4 * case.mesh.n_tets * per_point
+
+
+def _profile_traffic(kernel_src, name="jvp32_traffic.json", key="dram_bytes_per_jvp"):
+    """DRAM traffic per launch from a committed ncu summary, if still current."""
     try:
-        with open(os.path.join(ROOT, "profiles", "jvp32_traffic.json")) as f:
+        with open(os.path.join(ROOT, "profiles", name)) as f:
             d = json.load(f)
         h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
         if d.get("source_sha") == h:
-            return float(d["dram_bytes_per_jvp"])
+            return float(d[key])
     except Exception:
         pass
     return None
@@ -212,14 +235,26 @@ def run_gpu(args):
     value = ws * E * N * ops / t_total
     ms_step = t_total / args.steps * 1e3
 
-    # ---- dominant kernel: the FP32 tangent product, CUDA events on its stream
+    # ---- kernel timings.  The dominant kernel of the step (largest share of
+    # device time in the ncu launch list) is tau_dd_kernel, the tau of the FP64
+    # residual; its time and the tangent product's element kernel come from the
+    # library's own CUDA events on the launching stream (ts_stage_times).
+    R = 20
+    r64 = torch.empty_like(y)
+    t_tau, t_res64 = [], []
+    for _ in range(3):
+        ts.ts_residual(g.prob, y, r64)
+        st_ = ts.ts_stage_times(g.prob)
+        t_tau.append(st_["tau_ms"] / 1e3)
+        t_res64.append(st_["residual_element_ms"] / 1e3)
+    t_tau = float(np.mean(t_tau))
+    t_res64 = float(np.mean(t_res64))
     y32 = y.float().contiguous()
     ts.ts_residual(g.prob, y32, torch.empty_like(y32))
     v32 = torch.tensor(np.random.default_rng(0).standard_normal(y.shape), dtype=torch.float32, device="cuda")
     hv = torch.empty_like(v32)
     for _ in range(3):
         ts.ts_jvp(g.prob, v32, hv)
-    R = 20
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(R):
@@ -227,6 +262,11 @@ def run_gpu(args):
     e1.record(stream)
     torch.cuda.synchronize()
     t_jvp = e0.elapsed_time(e1) / 1e3 / R
+    t_jel = []
+    for _ in range(R):
+        ts.ts_jvp(g.prob, v32, hv)
+        t_jel.append(ts.ts_stage_times(g.prob)["jvp_element_ms"] / 1e3)
+    t_jel = float(np.mean(t_jel))
     # residual (tau refresh) in FP32 for the breakdown
     r32 = torch.empty_like(y32)
     e0.record(stream)
@@ -237,8 +277,14 @@ def run_gpu(args):
     t_res32 = e0.elapsed_time(e1) / 1e3 / 3
     peak, peak_kind = _peaks()
     alg = _jvp_bytes(case)
-    achieved = alg / t_jvp / 1e9
-    traffic = _profile_traffic(os.path.join(ROOT, "paper_2311_09465_gb300", "csrc", "jvp32.cuh"))
+    achieved = alg / t_jel / 1e9
+    csrc = os.path.join(ROOT, "paper_2311_09465_gb300", "csrc")
+    traffic = _profile_traffic(os.path.join(csrc, "jvp32.cuh"))
+    # FP32 issue peak: SMs x 128 FP32 lanes x the maximum SM clock
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    alu_peak = sms * 128 * _sm_max_mhz() * 1e6 / 1e12
+    tau_work = _tau_dd_instr(case)
+    tau_traffic = _profile_traffic(os.path.join(csrc, "tau_dd.cu"), "tau_dd_traffic.json", "dram_bytes_per_launch")
 
     # ---- end-to-end through the public API with host buffers
     y_host = torch.tensor(case.y0, dtype=torch.float64).pin_memory()
@@ -267,13 +313,22 @@ def run_gpu(args):
         "data": "synthetic seeded junction mesh and inflow (patient Fontan data not available)",
         "config": _config(case, {"parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"}),
         "e2e": e2e, "gpu_launches": int(launches),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "jvp32_kernel<7, LIN_A> (FP32 tangent product, one launch)",
-                     "algorithmic_bytes": alg, "launch_ms": t_jvp * 1e3, "peak_source": peak_kind},
+        "roofline": {"bound": "alu", "achieved": tau_work / t_tau / 1e12, "peak": alu_peak,
+                     "unit": "T FP32 instructions/s", "frac": tau_work / t_tau / 1e12 / alu_peak,
+                     "traffic": tau_traffic,
+                     "kernel": "tau_dd_kernel<7> (tau of the FP64 residual, double-float refinement)",
+                     "algorithmic_work": tau_work, "launch_ms": t_tau * 1e3,
+                     "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x {_sm_max_mhz():.0f} MHz"},
+        "roofline_tangent": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": traffic,
+                             "kernel": "jvp32_kernel<7, LIN_A> (FP32 tangent product, element pass)",
+                             "algorithmic_bytes": alg, "launch_ms": t_jel * 1e3,
+                             "product_ms": t_jvp * 1e3, "peak_source": peak_kind},
         "cpu_baseline": cpu,
         "clocks": clk,
-        "breakdown": {"jvp_fp32_ms": t_jvp * 1e3, "residual_fp32_ms": t_res32 * 1e3,
+        "breakdown": {"jvp_fp32_ms": t_jvp * 1e3, "jvp_element_kernel_ms": t_jel * 1e3,
+                      "tau_dd_ms": t_tau * 1e3, "residual_fp64_element_pass_ms": t_res64 * 1e3,
+                      "residual_fp32_ms": t_res32 * 1e3,
                       "solve_report": {k: rep[k] for k in ("steps", "matvecs", "t_residual", "t_jvp", "t_krylov")}},
         "time_to_residual_1e-8": ttr or None,
     }

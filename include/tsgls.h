@@ -300,6 +300,16 @@ const char* ts_version(void);
  * all streams); a diagnostic for counting launches inside a timed region. */
 int64_t ts_launch_count(void);
 
+/* Device time in milliseconds, from CUDA events on the call's stream, of
+ * out[0] the tau kernel (eq. 3D-tau) of the problem's last ts_residual,
+ * out[1] that residual's element pass (eq. Rmc, with the outlet terms) and
+ * out[2] the element kernel of its last single-launch FP32 tangent product
+ * (eq. K_mat; node pre-pass and boundary terms excluded); -1 where no such
+ * call has run.  Waits for those events.  A measurement aid with no
+ * counterpart in the paper.  out: caller-owned host array of 3 doubles.
+ * Returns 0, TS_ERR_ARG or TS_ERR_CUDA. */
+int ts_stage_times(ts_problem* pr, double* out);
+
 #ifdef __cplusplus
 }
 #endif

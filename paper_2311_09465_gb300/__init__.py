@@ -115,6 +115,7 @@ def lib() -> ctypes.CDLL:
     L.ts_last_error.restype = ctypes.c_char_p
     L.ts_version.restype = ctypes.c_char_p
     L.ts_launch_count.restype = ctypes.c_int64
+    L.ts_stage_times.argtypes = [vp, dp]
     _lib = L
     return L
 
@@ -135,6 +136,14 @@ def ts_version() -> str:
 
 def ts_launch_count() -> int:
     return int(lib().ts_launch_count())
+
+
+def ts_stage_times(prob) -> dict:
+    """Device milliseconds of the last residual's tau kernel and element pass and
+    of the last FP32 tangent product's element kernel (-1: not run yet)."""
+    out = (ctypes.c_double * 3)()
+    _check(lib().ts_stage_times(prob, out))
+    return {"tau_ms": out[0], "residual_element_ms": out[1], "jvp_element_ms": out[2]}
 
 
 def _stream_ptr(stream):

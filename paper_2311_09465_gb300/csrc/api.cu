@@ -102,6 +102,10 @@ struct ts_problem {
   float *d_v32 = nullptr, *d_w32 = nullptr;
   double *d_D = nullptr, *d_t = nullptr;      // preconditioner diagonal (inverted), temp
   cudaEvent_t ev_a = nullptr, ev_b = nullptr; // time of the tangent products in a solve
+  // stage times (ts_stage_times): tau start/end and element pass end of the
+  // last residual; element kernel start/end of the last FP32 tangent product
+  cudaEvent_t sev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  bool sev_res = false, sev_jvp = false;
   bool fast32 = true;    // FP32 products with the single-launch kernel (jvp32.cu)
   int tau64 = TS_TAU64_DOUBLEFLOAT;  // how the FP64 residual computes tau
 };
@@ -301,6 +305,7 @@ static int residual_impl(ts_problem* pr, const T* y, T* r, cudaStream_t st) {
   TS_TRY(lin_alloc(pr, l));
   const int64_t n = field_len(pr);
   TS_CUDA(cudaMemcpyAsync(l.u0, y, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  TS_CUDA(cudaEventRecord(pr->sev[0], st));
   int rc;
   if constexpr (sizeof(T) == 8) {
     if (pr->tau64 == TS_TAU64_JACOBI)
@@ -317,8 +322,11 @@ static int residual_impl(ts_problem* pr, const T* y, T* r, cudaStream_t st) {
                           (T)pr->p.C_I, pr->d_counter, st);
   }
   if (rc) return fail(TS_ERR_CUDA, "tau kernel launch failed");
+  TS_CUDA(cudaEventRecord(pr->sev[1], st));
   TS_CUDA(cudaMemsetAsync(r, 0, n * sizeof(T), st));
   TS_TRY(apply_colours<T, N>(pr, MODE_RESIDUAL, y, y, l, r, false, st));
+  TS_CUDA(cudaEventRecord(pr->sev[2], st));
+  pr->sev_res = true;
   TS_TRY(bneg_alloc(pr, l));
   TS_TRY(backflow_terms<T, N>(pr, l, y, true, 0, r, st));
   if constexpr (sizeof(T) == 4 && N <= J32_MAX_N) {
@@ -387,8 +395,9 @@ static int jvp_impl(ts_problem* pr, const T* v, T* hv, cudaStream_t st) {
     const J32Inst I{m->d_tets, m->d_geo32, (const float*)v, (const float*)l.u0t, (float*)l.vt,
                     (const float*)l.tau, (const float*)l.t0, pr->d_dmask, (float*)hv,
                     phys_of<float>(pr, true), m->E, m->V, N};
-    int rc = launch_jvp32<N>(mode, I, st);
+    int rc = launch_jvp32<N>(mode, I, st, pr->sev[3], pr->sev[4]);
     if (rc) return fail(TS_ERR_CUDA, "FP32 tangent kernel launch failed");
+    pr->sev_jvp = true;
     for (auto& o : pr->outlets)
       if (launch_outlet<T>(o.d_nodes, outlet_w<T>(o), (int)o.nodes.size(), (T)o.R, v, pr->d_dmask, 1,
                            hv, pr->C, st))
@@ -503,6 +512,25 @@ const char* ts_last_error(void) { return g_last_error.c_str(); }
 const char* ts_version(void) { return "tsgls-gb300 0.1 (sm_103a)"; }
 
 int64_t ts_launch_count(void) { return (int64_t)ts::launches_total(); }
+
+int ts_stage_times(ts_problem* pr, double* out) {
+  if (!pr || !out) return fail(TS_ERR_ARG, "ts_stage_times: NULL argument");
+  out[0] = out[1] = out[2] = -1.0;
+  float ms = 0.f;
+  if (pr->sev_res) {
+    TS_CUDA(cudaEventSynchronize(pr->sev[2]));
+    TS_CUDA(cudaEventElapsedTime(&ms, pr->sev[0], pr->sev[1]));
+    out[0] = ms;
+    TS_CUDA(cudaEventElapsedTime(&ms, pr->sev[1], pr->sev[2]));
+    out[1] = ms;
+  }
+  if (pr->sev_jvp) {
+    TS_CUDA(cudaEventSynchronize(pr->sev[4]));
+    TS_CUDA(cudaEventElapsedTime(&ms, pr->sev[3], pr->sev[4]));
+    out[2] = ms;
+  }
+  return 0;
+}
 
 int ts_mesh_load(const double* xyz_host, int64_t n_nodes, const int32_t* tets_host,
                  int64_t n_tets, const int32_t* bfaces_host, const int32_t* btag_host,
@@ -684,7 +712,10 @@ int ts_problem_create(const ts_mesh* mesh, const ts_params* params, ts_problem**
   {
   }
   if (dalloc(&pr->d_dmask, (size_t)mesh->V) || dalloc(&pr->d_counter, 1) ||
-      cudaEventCreate(&pr->ev_a) != cudaSuccess || cudaEventCreate(&pr->ev_b) != cudaSuccess) {
+      cudaEventCreate(&pr->ev_a) != cudaSuccess || cudaEventCreate(&pr->ev_b) != cudaSuccess ||
+      cudaEventCreate(&pr->sev[0]) != cudaSuccess || cudaEventCreate(&pr->sev[1]) != cudaSuccess ||
+      cudaEventCreate(&pr->sev[2]) != cudaSuccess || cudaEventCreate(&pr->sev[3]) != cudaSuccess ||
+      cudaEventCreate(&pr->sev[4]) != cudaSuccess) {
     ts_problem_free(pr);
     return TS_ERR_OOM;
   }
@@ -697,6 +728,8 @@ void ts_problem_free(ts_problem* pr) {
   if (!pr) return;
   if (pr->ev_a) cudaEventDestroy(pr->ev_a);
   if (pr->ev_b) cudaEventDestroy(pr->ev_b);
+  for (auto& e : pr->sev)
+    if (e) cudaEventDestroy(e);
   dfree(pr->d_dmask);
   dfree(pr->d_counter);
   for (auto& o : pr->outlets) {
@@ -991,8 +1024,8 @@ int ts_solve(ts_problem* pr, void* y_inout, const ts_solve_opts* opts, ts_solve_
     TS_TRY(dalloc(&pr->d_w, n));
     TS_TRY(dalloc(&pr->d_r, n));
     TS_TRY(dalloc(&pr->d_dy, n));
-    TS_TRY(dalloc(&pr->d_partial, (size_t)krylov_partial_blocks() * 128));
-    TS_TRY(dalloc(&pr->d_h, 3 * 130));
+    TS_TRY(dalloc(&pr->d_partial, (size_t)krylov_partial_blocks() * 130));
+    TS_TRY(dalloc(&pr->d_h, 3 * 130 + 2));
     TS_TRY(dalloc(&pr->d_v32, n));
     TS_TRY(dalloc(&pr->d_w32, n));
     TS_TRY(dalloc(&pr->d_D, n));
@@ -1095,16 +1128,19 @@ int ts_solve(ts_problem* pr, void* y_inout, const ts_solve_opts* opts, ts_solve_
         }
         TS_CUDA(cudaEventRecord(pr->ev_b, st));
         ++nmv;
-        // classical Gram-Schmidt, two passes, and the normalisation, all on the
-        // device: one host round trip per iteration returns the column
+        // classical Gram-Schmidt and the normalisation, all on the device: one
+        // host round trip per iteration returns the column.  The second pass
+        // runs only when the first removed more than half of |w|^2 (the test
+        // and the skip happen on the device; a skipped pass adds zeros)
         double* dh1 = pr->d_h;
         double* dh2 = pr->d_h + 130;
         double* dn2 = pr->d_h + 260;
-        for (int pass = 0; pass < 2; ++pass) {
-          double* dh = pass == 0 ? dh1 : dh2;
-          if (krylov_dots(V, n, k + 1, pr->d_w, n, pr->d_partial, dh, st)) return fail(TS_ERR_CUDA, "dots");
-          if (krylov_sub(pr->d_w, V, n, k + 1, dh, n, st)) return fail(TS_ERR_CUDA, "sub");
-        }
+        double* dskip = pr->d_h + 390;
+        if (krylov_dots(V, n, k + 1, pr->d_w, n, pr->d_partial, dh1, st, 1)) return fail(TS_ERR_CUDA, "dots");
+        if (krylov_sub(pr->d_w, V, n, k + 1, dh1, n, st)) return fail(TS_ERR_CUDA, "sub");
+        if (krylov_reorth_test(dh1, k + 1, dskip, st)) return fail(TS_ERR_CUDA, "reorth test");
+        if (krylov_dots(V, n, k + 1, pr->d_w, n, pr->d_partial, dh2, st, 0, dskip)) return fail(TS_ERR_CUDA, "dots");
+        if (krylov_sub(pr->d_w, V, n, k + 1, dh2, n, st, dskip)) return fail(TS_ERR_CUDA, "sub");
         if (krylov_dots(pr->d_w, n, 1, pr->d_w, n, pr->d_partial, dn2, st)) return fail(TS_ERR_CUDA, "norm");
         if (vec_normalise(V + (int64_t)(k + 1) * n, pr->d_w, dn2, n, st)) return fail(TS_ERR_CUDA, "normalise");
         double hh[3 * 130];

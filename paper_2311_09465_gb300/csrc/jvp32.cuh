@@ -899,10 +899,14 @@ static int j32_upload_impl(const float* host_all, int (*global_offset)(int)) {
 }
 
 template <int N>
-int launch_jvp32(int mode, const J32Inst& I, cudaStream_t st) {
+int launch_jvp32(int mode, const J32Inst& I, cudaStream_t st, cudaEvent_t e_before, cudaEvent_t e_after) {
   // the node pre-pass samples v and clears out; the element pass adds to out
   if (launch_node_samples_impl<N>(I.v, I.dmask, I.vt, I.out, I.n_nodes, st)) return -2;
-  return launch_jvp32_impl<N>(mode, I, st);
+  if (e_before && cudaEventRecord(e_before, st) != cudaSuccess) return -2;
+  const int rc = launch_jvp32_impl<N>(mode, I, st);
+  if (rc) return rc;
+  if (e_after && cudaEventRecord(e_after, st) != cudaSuccess) return -2;
+  return 0;
 }
 
 template <int N>

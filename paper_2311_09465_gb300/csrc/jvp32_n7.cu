@@ -6,7 +6,7 @@ namespace ts {
 
 int j32_upload_n7(const float* host_all) { return j32_upload_impl(host_all, dft_constant_offset); }
 
-template int launch_jvp32<7>(int, const J32Inst&, cudaStream_t);
+template int launch_jvp32<7>(int, const J32Inst&, cudaStream_t, cudaEvent_t, cudaEvent_t);
 template int launch_node_samples<7>(const float*, float*, int64_t, cudaStream_t);
 
 }  // namespace ts

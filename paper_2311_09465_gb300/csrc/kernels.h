@@ -83,8 +83,10 @@ int j32_upload_batch(const float* host_all);
 
 // FP32 tangent product (jvp32.cuh): a node pre-pass (v sampled into I.vt,
 // I.out cleared) and one element launch
+// (with e_before / e_after: events recorded around the element launch)
 template <int N>
-int launch_jvp32(int mode, const J32Inst& I, cudaStream_t st);
+int launch_jvp32(int mode, const J32Inst& I, cudaStream_t st, cudaEvent_t e_before = nullptr,
+                 cudaEvent_t e_after = nullptr);
 // u0 velocity at the nodes as time samples [V][K] float4 (x, y, z, 0)
 template <int N>
 int launch_node_samples(const float* u0, float* u0t, int64_t V, cudaStream_t st);
@@ -98,10 +100,16 @@ int j32_upload_n7(const float* host_all);
 constexpr int J32_MAX_N = 7;   // largest N with the single-launch FP32 kernel
 
 // FP64 Krylov helpers (krylov.cu)
+// h_out[j] = basis_j . w (j < nvec), with self also h_out[nvec] = w . w;
+// with *skip != 0 (device flag) every h_out is 0 and nothing is read
 int krylov_dots(const double* basis, int64_t ld, int nvec, const double* w, int64_t n,
-                double* partial, double* h_out, cudaStream_t st);
+                double* partial, double* h_out, cudaStream_t st, int self = 0,
+                const double* skip = nullptr);
+// w -= sum_j h_j basis_j, nothing when *skip != 0
 int krylov_sub(double* w, const double* basis, int64_t ld, int nvec, const double* h, int64_t n,
-               cudaStream_t st);
+               cudaStream_t st, const double* skip = nullptr);
+// flag = 1 when the second Gram-Schmidt pass can be skipped (see krylov.cu)
+int krylov_reorth_test(const double* h, int nvec, double* flag, cudaStream_t st);
 int krylov_combine(double* x, const double* basis, int64_t ld, int nvec, const double* coef,
                    int64_t n, cudaStream_t st);
 int vec_scale(double* out, const double* in, double a, int64_t n, cudaStream_t st);

@@ -24,24 +24,46 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// partial[j * gridDim.x + b] = sum over block b's chunk of basis_j . w
+// partial[j * gridDim.x + b] = sum over block b's chunk of basis_j . w for
+// j < nvec (nvec >= 1), and with self != 0 also row nvec = w . w.  With *skip != 0 the
+// block writes zeros and reads nothing (a second Gram-Schmidt pass that is not
+// needed).  On GB300 the multiply-adds run on the FP64 pipe; of the layouts
+// measured on the 2.1M-unknown junction field (chunks x vector groups, a
+// warp-level transposed GEMV, 16-byte loads) this one streams fastest.
 __global__ void __launch_bounds__(RED_THREADS) dots_kernel(const double* __restrict__ basis,
                                                            int64_t ld, int nvec,
                                                            const double* __restrict__ w,
-                                                           int64_t n, double* __restrict__ partial) {
+                                                           int64_t n, double* __restrict__ partial,
+                                                           int self, const double* __restrict__ skip) {
+  const int nout = nvec + (self ? 1 : 0);
+  if (skip != nullptr && *skip != 0.0) {
+    for (int j = threadIdx.x; j < nout; j += blockDim.x) partial[(int64_t)j * gridDim.x + blockIdx.x] = 0.0;
+    return;
+  }
   __shared__ double red[RED_THREADS / 32][4];
   const int64_t chunk = ((n + gridDim.x - 1) / gridDim.x + 1) & ~(int64_t)1;
   const int64_t i0 = (int64_t)blockIdx.x * chunk;
   const int64_t i1 = i0 + chunk < n ? i0 + chunk : n;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double self_acc = 0;
   for (int j0 = 0; j0 < nvec; j0 += 4) {
     const int nj = nvec - j0 < 4 ? nvec - j0 : 4;
     double acc[4] = {0, 0, 0, 0};
-    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-      const double wi = w[i];
+    if (self && j0 == 0) {
+      for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const double wi = w[i];
 #pragma unroll
-      for (int jj = 0; jj < 4; ++jj)
-        if (jj < nj) acc[jj] += basis[(int64_t)(j0 + jj) * ld + i] * wi;
+        for (int jj = 0; jj < 4; ++jj)
+          if (jj < nj) acc[jj] += basis[(int64_t)(j0 + jj) * ld + i] * wi;
+        self_acc += wi * wi;
+      }
+    } else {
+      for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const double wi = w[i];
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj)
+          if (jj < nj) acc[jj] += basis[(int64_t)(j0 + jj) * ld + i] * wi;
+      }
     }
 #pragma unroll
     for (int jj = 0; jj < 4; ++jj) {
@@ -49,12 +71,22 @@ __global__ void __launch_bounds__(RED_THREADS) dots_kernel(const double* __restr
       if (lane == 0) red[warp][jj] = s;
     }
     __syncthreads();
-    if (threadIdx.x < nj) {
+    if ((int)threadIdx.x < nj) {
       double s = 0;
       for (int k = 0; k < RED_THREADS / 32; ++k) s += red[k][threadIdx.x];
       partial[(int64_t)(j0 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
     }
     __syncthreads();
+  }
+  if (self) {   // row nvec: w . w (accumulated with the first group)
+    const double s = warp_sum(self_acc);
+    if (lane == 0) red[warp][0] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0;
+      for (int k = 0; k < RED_THREADS / 32; ++k) t += red[k][0];
+      partial[(int64_t)nvec * gridDim.x + blockIdx.x] = t;
+    }
   }
 }
 
@@ -70,19 +102,69 @@ __global__ void sum_partials_kernel(const double* __restrict__ partial, int nblk
 }
 
 int krylov_dots(const double* basis, int64_t ld, int nvec, const double* w, int64_t n,
-                double* partial, double* h_out, cudaStream_t st) {
+                double* partial, double* h_out, cudaStream_t st, int self, const double* skip) {
+  const int nout = nvec + (self ? 1 : 0);
   count_launches(2);
-  dots_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(basis, ld, nvec, w, n, partial);
-  sum_partials_kernel<<<(nvec + 3) / 4, 128, 0, st>>>(partial, RED_BLOCKS, nvec, h_out);
+  dots_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(basis, ld, nvec, w, n, partial, self, skip);
+  sum_partials_kernel<<<(nout + 3) / 4, 128, 0, st>>>(partial, RED_BLOCKS, nout, h_out);
   return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
-// w -= sum_j h_j basis_j
+// Second Gram-Schmidt pass needed?  h holds the first pass's coefficients
+// h[0..nvec) and |w|^2 before it at h[nvec]; after the pass |w'|^2 =
+// |w|^2 - sum h_j^2.  The pass is skipped (flag 1) when |w'|^2 >= |w|^2 / 2:
+// a vector that lost less than half its length to the projection is
+// orthogonal to working accuracy after one pass ("twice is enough").
+__global__ void reorth_test_kernel(const double* __restrict__ h, int nvec, double* __restrict__ flag) {
+  double s = 0;
+  for (int j = threadIdx.x; j < nvec; j += 32) s += h[j] * h[j];
+  s = warp_sum(s);
+  if (threadIdx.x == 0) {
+    const double w2 = h[nvec];
+    *flag = (w2 > 0 && w2 - s >= 0.5 * w2) ? 1.0 : 0.0;
+  }
+}
+
+int krylov_reorth_test(const double* h, int nvec, double* flag, cudaStream_t st) {
+  count_launches(1);
+  reorth_test_kernel<<<1, 32, 0, st>>>(h, nvec, flag);
+  return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+// w -= sum_j h_j basis_j (nothing when *skip != 0)
 __global__ void sub_kernel(double* __restrict__ w, const double* __restrict__ basis, int64_t ld,
-                           int nvec, const double* __restrict__ h, int64_t n) {
+                           int nvec, const double* __restrict__ h, int64_t n,
+                           const double* __restrict__ skip) {
+  if (skip != nullptr && *skip != 0.0) return;
   extern __shared__ double sh[];
   for (int j = threadIdx.x; j < nvec; j += blockDim.x) sh[j] = h[j];
   __syncthreads();
+  const bool vec = ((ld | n) & 1) == 0 && ((reinterpret_cast<uintptr_t>(basis) | reinterpret_cast<uintptr_t>(w)) & 15) == 0;
+  if (vec) {
+    double2* w2 = reinterpret_cast<double2*>(w);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n / 2;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      double2 acc = w2[i];
+      int j = 0;
+      for (; j + 3 < nvec; j += 4) {
+        double2 b[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) b[u] = reinterpret_cast<const double2*>(basis + (int64_t)(j + u) * ld)[i];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          acc.x = fma(-sh[j + u], b[u].x, acc.x);
+          acc.y = fma(-sh[j + u], b[u].y, acc.y);
+        }
+      }
+      for (; j < nvec; ++j) {
+        const double2 b = reinterpret_cast<const double2*>(basis + (int64_t)j * ld)[i];
+        acc.x = fma(-sh[j], b.x, acc.x);
+        acc.y = fma(-sh[j], b.y, acc.y);
+      }
+      w2[i] = acc;
+    }
+    return;
+  }
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     double acc = w[i];
@@ -112,9 +194,9 @@ static int grid_for(int64_t n) {
 }
 
 int krylov_sub(double* w, const double* basis, int64_t ld, int nvec, const double* h, int64_t n,
-               cudaStream_t st) {
+               cudaStream_t st, const double* skip) {
   count_launches(1);
-  sub_kernel<<<grid_for(n), 256, nvec * sizeof(double), st>>>(w, basis, ld, nvec, h, n);
+  sub_kernel<<<grid_for(n), 256, nvec * sizeof(double), st>>>(w, basis, ld, nvec, h, n, skip);
   return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
