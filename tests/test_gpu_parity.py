@@ -54,7 +54,9 @@ CASES = {
     "pipe_N7": lambda: _pipe(7, nc=2, nr=2, nz=4),
     "junction_N2": lambda: _junction(2),
     "junction_N4": lambda: _junction(4),
+    "pipe_N5": lambda: _pipe(5, nc=2, nr=1, nz=3),
     "pipe_N10": lambda: _pipe(10, nc=2, nr=1, nz=2),
+    "pipe_N15": lambda: _pipe(15, nc=2, nr=1, nz=2),
 }
 
 
@@ -75,8 +77,11 @@ def test_residual_matches_oracle(torch, name, prec):
 
 @pytest.mark.parametrize("variant", ["paper", "frozen", "lin_a"])
 @pytest.mark.parametrize("prec", [64, 32])
-@pytest.mark.parametrize("name", ["pipe_N3", "junction_N2", "pipe_N7"])
+@pytest.mark.parametrize("name", ["pipe_N1", "pipe_N3", "junction_N2", "junction_N4", "pipe_N5", "pipe_N7",
+                                  "pipe_N10", "pipe_N15"])
 def test_jvp_matches_oracle(torch, name, variant, prec):
+    # N <= 7 in FP32: the single-launch kernel (node pre-pass, staged tau,
+    # atomics); N = 10, 15 and FP64: the colour-ordered element kernel
     case = CASES[name]()
     dt = 0.7
     y = _state(case, seed=2)
