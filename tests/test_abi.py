@@ -51,3 +51,42 @@ def test_python_binding_mirrors_the_abi():
     import paper_2311_09465_gb300 as ts
     for n in _declared():
         assert hasattr(ts, n), n
+
+
+def _c_layout(tmp_path, structs):
+    """sizeof and field offsets of the header's structs, from the C compiler."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "tsgls.h"', "int main(void) {"]
+    for name, fields in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for f in fields:
+            lines.append(f'  printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    res = {}
+    for line in out.splitlines():
+        name, field, val = line.split()
+        res[(name, field)] = int(val)
+    return res
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    # the ctypes mirrors of ts_params, ts_solve_opts and ts_solve_report have the
+    # C header's size and field offsets (a field added on one side only fails here)
+    import paper_2311_09465_gb300 as ts
+    mirrors = {"ts_params": ts.ts_params, "ts_solve_opts": ts.ts_solve_opts,
+               "ts_solve_report": ts.ts_solve_report}
+    structs = {name: [f for f, _ in cls._fields_] for name, cls in mirrors.items()}
+    c = _c_layout(tmp_path, structs)
+    for name, cls in mirrors.items():
+        assert c[(name, "size")] == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert c[(name, f)] == getattr(cls, f).offset, (name, f)
