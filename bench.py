@@ -172,24 +172,34 @@ def _profile_traffic(kernel_src, name="jvp32_traffic.json", key="dram_bytes_per_
     return None
 
 
-def _dist():
+def _dist(backend="nccl"):
+    """Process group of a torchrun launch (RANK, WORLD_SIZE, MASTER_* from the
+    environment); None on one rank.  Each rank runs its own replica of the
+    workload (no data-path collective)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if ws > 1:
         import torch.distributed as dist
-        backend = "nccl"
         dist.init_process_group(backend=backend)
         return dist, rank, ws
     return None, rank, ws
 
 
 def _max_over_ranks(dist, x):
+    """The largest x over the ranks (the job's time is its slowest rank's)."""
     if dist is None:
         return x
     import torch
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def _job_rate(ws, n_tets, n_modes, ops, seconds):
+    """Whole-job element-mode evaluations per second: every rank runs the same
+    replica, so the units processed are ws times one rank's."""
+    return ws * n_tets * n_modes * ops / seconds
 
 
 def run_gpu(args):
@@ -232,7 +242,7 @@ def run_gpu(args):
     t_total = ev0.elapsed_time(ev1) / 1e3
     t_total = _max_over_ranks(dist, t_total)
     ops = rep["matvecs"] + rep["steps"] + 1          # tangent products + residuals
-    value = ws * E * N * ops / t_total
+    value = _job_rate(ws, E, N, ops, t_total)
     ms_step = t_total / args.steps * 1e3
 
     # ---- kernel timings.  The dominant kernel of the step (largest share of
@@ -297,7 +307,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     t_e2e = _max_over_ranks(dist, time.perf_counter() - t0)
     ops_e = rep_e["matvecs"] + rep_e["steps"] + 1
-    e2e = {"value": ws * E * N * ops_e / t_e2e, "unit": "element-mode evals/s",
+    e2e = {"value": _job_rate(ws, E, N, ops_e, t_e2e), "unit": "element-mode evals/s",
            "h2d_bytes_per_step": int(y_host.numel() * 8 / args.steps),
            "d2h_bytes_per_step": int(y_host.numel() * 8 / args.steps)}
 
