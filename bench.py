@@ -562,6 +562,84 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_sweep(args):
+    """Mode sweep on the bench junction (N = 3, 7, 15; one JSON line).
+
+    Per N: device time of the FP32 tangent product (the single-launch kernel
+    for N <= 7, the colour-ordered one for N = 15) and of the FP64 residual,
+    element-mode evaluations per second and achieved GB/s of the product
+    (algorithmic bytes as in the bench line), and the relative L2 error of each
+    Fourier mode n of the FP32 product and of the FP32 and FP64 residuals
+    against the FP64 oracle, over seeded sample nodes whose rows the oracle
+    computes exactly from the elements that touch them."""
+    import torch
+
+    import paper_2311_09465_gb300 as ts
+    from oracle import operator as op
+    from workloads import cases, meshgen as mg
+
+    mesh = mg.junction(h=0.123, seed=1)
+    rng = np.random.default_rng(23)
+    nodes = np.unique(np.concatenate([rng.choice(mesh.n_nodes, 24, replace=False)] + [
+        rng.choice(np.nonzero(cases.nodes_with_tag(mesh, t))[0], 3, replace=False)
+        for t in (mg.TAG_WALL, mg.TAG_INLET1, mg.TAG_OUTLET1)]))
+    peak, peak_kind = _peaks()
+    out = []
+    for N in (3, 7, 15):
+        case = cases.junction_case(N=N, Re=500.0, Wo=10.0, wave_seed=100, resistance=1.0, mesh=mesh,
+                                   amp=WAVE_AMP)
+        y = case.y0 + 0.3 * cases.random_state(mesh, N, seed=21)
+        y[case.dirichlet_mask, 0:3] = case.y0[case.dirichlet_mask, 0:3]
+        y[:, :, 0, 1] = 0.0
+        v = cases.random_state(mesh, N, seed=22, smooth=False)
+        prob = op.problem_from_case(case)
+        lin = op.linearize(prob, y, elems=op.element_sample_for_nodes(prob, nodes))
+        r_ref = op.apply(prob, lin, y, "frozen")[nodes]
+        mc = case.c1 * case.rho / args.dt
+        hv_ref = op.apply(prob, lin, v, "lin_a", mask_dirichlet_input=True, mass_coef=mc)[nodes]
+        g = ts.GLSProblem(case, variant="lin_a", dt_pseudo=args.dt)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        y64 = torch.tensor(y, dtype=torch.float64, device="cuda")
+        r64 = g.residual(y64)
+        e0.record()
+        for _ in range(2):
+            r64 = g.residual(y64)
+        e1.record()
+        torch.cuda.synchronize()
+        t_res64 = e0.elapsed_time(e1) / 2e3
+        r64 = r64.cpu().numpy()[nodes]
+        r32 = g.residual(y64.float()).cpu().double().numpy()[nodes]
+        v32 = torch.tensor(v, dtype=torch.float32, device="cuda")
+        hv = g.jvp(v32)
+        e0.record()
+        for _ in range(10):
+            hv = g.jvp(v32)
+        e1.record()
+        torch.cuda.synchronize()
+        t_jvp = e0.elapsed_time(e1) / 1e4
+        hv = hv.cpu().double().numpy()[nodes]
+
+        def per_mode(got, ref):
+            errs = []
+            for n in range(N):
+                d = got[:, :, n, :] - ref[:, :, n, :]
+                errs.append(float(np.linalg.norm(d) / max(np.linalg.norm(ref[:, :, n, :]), 1e-300)))
+            return errs
+
+        byts = _jvp_bytes(case)
+        out.append({"N": N, "K": 3 * N - 2,
+                    "tangent_fp32_ms": t_jvp * 1e3, "tangent_element_mode_evals_per_s": case.mesh.n_tets * N / t_jvp,
+                    "tangent_gbs": byts / t_jvp / 1e9, "tangent_frac_of_hbm": byts / t_jvp / 1e9 / peak,
+                    "residual_fp64_ms": t_res64 * 1e3,
+                    "rel_l2_per_mode_tangent_fp32": per_mode(hv, hv_ref),
+                    "rel_l2_per_mode_residual_fp32": per_mode(r32, r_ref),
+                    "rel_l2_per_mode_residual_fp64": per_mode(r64, r_ref)})
+        g.close()
+    print(json.dumps({"sweep": "modes", "workload": f"junction {mesh.n_tets} tets, Re 500, Wo 10",
+                      "sample_nodes": int(nodes.size), "peak_gbs": peak, "peak_source": peak_kind,
+                      "rows": out}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -575,8 +653,12 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=400)
     ap.add_argument("--ref-sample", type=int, default=200)
+    ap.add_argument("--sweep", action="store_true",
+                    help="mode sweep N = 3, 7, 15 on the junction (its own JSON line) instead of the bench")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.sweep:
+        run_sweep(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)
