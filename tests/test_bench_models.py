@@ -1,0 +1,46 @@
+"""The algorithmic models behind the bench line's roofline entries, pinned to
+the figures quoted in the design notes and the ncu summaries (CPU only)."""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+class _Mesh:
+    def __init__(self, n_tets, n_nodes):
+        self.n_tets, self.n_nodes = n_tets, n_nodes
+
+
+class _Case:
+    def __init__(self, N, n_tets, n_nodes):
+        self.N, self.mesh = N, _Mesh(n_tets, n_nodes)
+
+
+def test_tangent_bytes_at_the_junction():
+    import bench
+    # v, u0/p0 and Hv (8N values per node, FP32), connectivity, coordinates,
+    # packed tau (4 points x 91 entries) and tau L (4 x 3 x 14) per element
+    c = _Case(7, 187_989, 38_250)
+    V, E = 38_250, 187_989
+    expect = 3 * V * 56 * 4 + 16 * E + 12 * V + E * 4 * 91 * 4 + E * 4 * 3 * 14 * 4
+    assert bench._jvp_bytes(c) == expect == 429_211_416
+
+
+def test_tau_dd_instruction_model():
+    import bench
+    # per point at N = 7 (n = 13, t = 91): 15 instructions per double-float
+    # multiply-add for M (3 t n), the second Gram matrix, B and tau (t n each)
+    # and the four full products (n^3 each), 13 for the first Gram matrix (t n)
+    per_point = 15 * (3 * 91 * 13 + 3 * 91 * 13 + 4 * 13 ** 3) + 13 * 91 * 13
+    assert per_point == 253_669
+    assert bench._tau_dd_instr(_Case(7, 10, 5)) == 4 * 10 * per_point
+    # N = 1: one mode, n = t = 1
+    assert bench._tau_dd_instr(_Case(1, 1, 4)) == 4 * (15 * (6 + 4) + 13)
+
+
+def test_job_rate_counts_every_replica():
+    import bench
+    assert bench._job_rate(1, 100, 7, 31, 2.0) == 100 * 7 * 31 / 2.0
+    assert bench._job_rate(4, 100, 7, 31, 2.0) == 4 * bench._job_rate(1, 100, 7, 31, 2.0)
