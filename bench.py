@@ -364,7 +364,7 @@ def _time_to_residual(ts, torch, case, g, args):
     """Full solves from the paper's initial guess to ||r|| <= 1e-8 r_ref."""
     from workloads import cases, meshgen as mg
     out = {}
-    # configs[0] geometry: Womersley pipe (R 1, L 5, ~9.6k tets), N = 3, Re 100, Wo 5
+    # the Womersley pipe (R 1, L 5, ~9.6k tets), N = 3, Re 100, Wo 5
     pipe = cases.pipe_case(N=3, Re=100.0, Wo=5.0, mesh=mg.pipe(nc=4, nr=4, nz=20))
     res = {}
     # mixed: FP32 tangent products, FP64 GMRES, outer residual with double-float tau;

@@ -7,7 +7,7 @@
 // f a fully connected tanh network from inflow coefficients, Re and Wo to the
 // normalised POD coefficients, trained with Adam (Kingma & Ba 2015) on
 // solves of the method itself.  The solver then iterates to the same
-// tolerance as from the plain guess, so the plain method judges the result.
+// tolerance as from the plain guess: the converged field is the plain method's.
 //
 // Every product is one FP32 tiled GEMM kernel with a fused epilogue (bias,
 // tanh, or the tanh derivative of the backward pass); the problem sizes
