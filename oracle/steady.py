@@ -15,8 +15,11 @@ Momentum (steady, second derivatives dropped):
   R^c_a    = int N_a du_i/dx_i + int (1/rho) dN_a/dx_i tau r_i  (PSPG)
 
 Parity: this function is itself the pin for the spectral residual's
-mode-0 limit; it is checked by hand-computable special cases in
-tests/test_oracle_operator.py (u = 0 Stokes limit, constant fields).
+mode-0 limit.  It is pinned on its own by closed forms per element in
+tests/test_oracle_steady.py, assembled with independently computed geometry:
+the u = 0 Stokes limit (pressure and PSPG terms), uniform flow with a linear
+pressure (SUPG and PSPG with a constant tau), and the Galerkin terms with the
+stabilisation switched off (exact P1 mass matrix, stiffness, divergence).
 """
 from __future__ import annotations
 

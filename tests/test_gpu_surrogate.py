@@ -85,11 +85,15 @@ def test_adam_steps_match_oracle(torch):
 def test_pod_basis_and_coefficients_match_oracle(torch):
     rng = np.random.default_rng(5)
     S, n = 12, 5003                           # ragged against tiles and split-K chunks
-    Y = rng.standard_normal((S, 4)) @ rng.standard_normal((4, n)) + 0.05 * rng.standard_normal((S, n))
+    # eight directions with well separated energies (consecutive singular values
+    # differ by >= 25%), so every basis vector is unique up to its sign
+    coef = rng.standard_normal((S, 8)) * (4.0 * 0.6 ** np.arange(8))
+    Y = coef @ rng.standard_normal((8, n)) + 1e-4 * rng.standard_normal((S, n))
     Y += 3.0
     s = _sur(n_out=8, n_dof=n)
     sigma = s.fit_basis(to_dev(Y, torch.float64))
     mean, Phi, sig_ref = sg.pod_basis(Y, 8)
+    assert np.min(sig_ref[:-1] / sig_ref[1:]) > 1.25
     assert len(sigma) == 8
     assert rel_l2(sigma, sig_ref) <= 1e-4
     A = to_np(s.coefficients(to_dev(Y, torch.float64)))
@@ -99,8 +103,8 @@ def test_pod_basis_and_coefficients_match_oracle(torch):
         k = np.argmax(np.abs(A_ref[:, j]))
         if np.sign(A[k, j]) != np.sign(A_ref[k, j]):
             A[:, j] *= -1
-    # the dominant directions are well separated; the noise directions less so
-    assert rel_l2(A[:, :4], A_ref[:, :4]) <= 1e-4, rel_l2(A[:, :4], A_ref[:, :4])
+    for j in range(8):
+        assert rel_l2(A[:, j], A_ref[:, j]) <= 1e-4, (j, rel_l2(A[:, j], A_ref[:, j]))
 
 
 def _pipe_sample(rng, mesh):
