@@ -51,6 +51,10 @@ extern "C" {
 #define TS_BC_RESISTANCE 3   /* h_n = -R Q_n, Q_n = int u_n . n (per mode) */
 #define TS_BC_BACKFLOW   4   /* backflow stabilisation with coefficient beta in [0,1] */
 
+/* inflow profiles for ts_set_inlet */
+#define TS_PROFILE_PARABOLIC 1 /* 2 U_n (1 - r^2/R^2), U_n = Q_n / (pi R^2)                   */
+#define TS_PROFILE_WOMERSLEY 2 /* fully developed pulsatile pipe flow per mode (mean U_n)    */
+
 /* tangent variants for ts_jvp / ts_solve (eq. K_mat) */
 #define TS_JVP_PAPER   0   /* A, tau frozen; LS parts of G_i, D_j dropped (section 2.5.2) */
 #define TS_JVP_FROZEN  1   /* A, tau frozen; all blocks of eq. (K_mat)                    */
@@ -90,9 +94,15 @@ typedef struct {
   double eps_ls;       /* GMRES relative tolerance (0.05 in section 2.4, remark 6)     */
   int    max_matvec;   /* per linear solve (10000 in section 3.2)                      */
   int    verbose;      /* print one line per step to stderr                            */
-  int    precond;      /* 0: none; 1: right diagonal scaling by an approximate diag(H)
-                          (viscous + mass + scalar-tau LS terms per node; changes the
-                          GMRES path only, never the converged field)                  */
+  int    precond;      /* right preconditioner of GMRES (changes the GMRES path only,
+                          never the converged field): 0 none; 1 diagonal scaling by an
+                          approximate diag(H) (viscous + mass + scalar-tau LS terms per
+                          node); 2 nodal block Jacobi: the inverted 8N x 8N diagonal
+                          blocks of the tangent at the current state (ts_block_diagonal),
+                          rebuilt every pseudo-time step; 3 symmetric block Gauss-Seidel:
+                          a forward and a backward sweep over a colouring of the node
+                          graph with the assembled paper-variant blocks (ts_assemble)
+                          off the diagonal and the inverted blocks of 2 on it          */
   double ser;          /* > 0: pseudo-time step grows as dt_k = dt_0 (|r_0|/|r_k|)^ser,
                           |r_0| = r_ref when given, else the first residual norm
                           (switched evolution relaxation; dt_0 = the problem's
@@ -121,6 +131,7 @@ typedef struct {
   int    hist_len;      /* entries written to hist                              */
   double hist[512];     /* ||r||/r_ref after each step (rejected ones included) */
   int    rejected;      /* steps undone by the reject test                      */
+  double t_precond;     /* seconds building the preconditioner (precond 1 or 2) */
 } ts_solve_report;
 
 /* Copies a tetrahedral mesh to the device and precomputes per-element shape
@@ -168,6 +179,36 @@ int  ts_problem_option(ts_problem* prob, int key, int value);
  *   value * Q_n * int N_A n_i on that outlet (a rank-one coupling per mode). */
 int  ts_set_bc(ts_problem* prob, int tag, int kind, double value);
 
+/* Inflow boundary data (section 2.4: the Dirichlet data g are expanded in the
+ * same Fourier modes as the unknowns, eq. upgh_def, g_n = (1/T) int g e^{-i n w t};
+ * section 3.1 prescribes a parabolic inlet profile scaled by the flow waveform).
+ * The boundary triangles with this tag form a circular inlet; the library
+ * takes its inflow direction from their area-weighted normal (pointing into
+ * the domain), and its centre and radius R from a least-squares circle
+ * (Kasa's algebraic fit) through the rim: the tag's nodes that also lie on
+ * triangles of other tags.  For each mode n = 0..N-1 the velocity at an
+ * inlet node at distance r from the axis is w_n(r) times the inflow
+ * direction, with w_n the profile of mean velocity U_n = Q_n / (pi R^2):
+ *   TS_PROFILE_PARABOLIC  w_n = 2 U_n (1 - r^2/R^2)
+ *   TS_PROFILE_WOMERSLEY  w_0 parabolic; w_n = U_n [1 - J0(L r/R)/J0(L)] /
+ *                         [1 - 2 J1(L)/(L J0(L))], L = i^{3/2} alpha_n,
+ *                         alpha_n = R sqrt(n omega rho/mu) (Womersley 1955; J0, J1
+ *                         from their power series, adequate for alpha_n <= 15)
+ * Rim nodes keep zero velocity (they belong to the wall).  All nodes of the
+ * tag become Dirichlet velocity nodes (as ts_set_bc with TS_BC_DIRICHLET).
+ *   Qn_host  [N][2] flow-rate coefficients (re, im) of modes 0..N-1, copied;
+ *            Im(Q_0) is ignored (the mean flow is real, section 3.3)
+ * A second call for the same tag replaces the first.  TS_ERR_ARG for an
+ * unknown profile, a tag without triangles, or a rim of fewer than 3 nodes. */
+int  ts_set_inlet(ts_problem* prob, int tag, const double* Qn_host, int profile);
+/* Geometry ts_set_inlet derived for a tag: out_host[0..2] centre, [3..5] unit
+ * inflow direction, [6] radius.  TS_ERR_ARG if the tag has no inlet data. */
+int  ts_inlet_info(const ts_problem* prob, int tag, double* out_host);
+/* The paper's initial guess (section 2.4): zero velocity and pressure
+ * everywhere except the inlet Dirichlet data of every ts_set_inlet tag.
+ * y: caller-owned device field, precision 32 (float) or 64 (double). */
+int  ts_initial_guess(ts_problem* prob, void* y, int precision, void* stream);
+
 /* Discrete residual r(y) of eq. (Rmc), section 2.4, for the caller's state y
  * (device, layout above, precision 32 or 64).  Momentum rows of Dirichlet
  * nodes and Im(mode 0) are zero.  Also freezes the linearisation used by
@@ -182,20 +223,70 @@ int  ts_residual(ts_problem* prob, const void* y, void* r, int precision, void* 
  * forbids new device allocations after set-up, or a host that has handed all
  * free device memory to another runtime.  It computes the same r(y) as
  * ts_residual(..., 32, ...) but keeps its intermediate data (tau per
- * quadrature point, tau L and the DFT tables) in one fixed 32 MiB device array
- * compiled into this library, which every GPU that loads the library holds
- * until the process exits.  y and r are caller-owned FP32 device fields; r is
- * overwritten.  Limits: (2(3N-2)(2N) + E*4*ntau + E*12*2N) floats, each part
- * rounded up to 64, must fit in 32 MiB (ntau = (2N-1)N rounded up to a
- * multiple of 4); larger meshes return TS_ERR_ARG with the sizes in the
- * message.  It does not refresh the linearisation state used by ts_jvp.
- * The first call on a device looks up the array's device address with that
- * device current; make that first call before any stream capture.  Every call
- * reuses the same array, so calls whose GPU work overlaps (other streams,
- * other host threads on the same device) race on it and must be serialised
- * by the caller.  Nothing in the array needs clearing between calls: each
- * call writes every part it reads.  Calls no cudaMalloc or cudaFree. */
+ * quadrature point and tau L) in one fixed 32 MiB device array compiled into
+ * this library, and reads its DFT tables from a second, 19 KB one.
+ * ts_problem_create sets these up on the current device (it resolves both
+ * arrays, which loads them also under CUDA's lazy module loading, writes the
+ * tables once per device and loads the two kernels this call launches), so a
+ * call only launches kernels and clears r; every GPU on which a problem was
+ * created holds the arrays until the process exits.  y and r are caller-owned
+ * FP32 device fields; r is overwritten.  Limits: (E*4*ntau rounded up to a
+ * multiple of 64) + E*12*2N floats must fit in 32 MiB (ntau = (2N-1)N rounded
+ * up to a multiple of 4): about 15k tetrahedra at N = 7, 61k at N = 3; larger
+ * meshes return TS_ERR_ARG with the sizes in the message.  It does not refresh
+ * the linearisation state used by ts_jvp, and problems with backflow faces
+ * return TS_ERR_ARG.  Every call reuses the same array, so calls whose GPU
+ * work overlaps (other streams, other host threads on the same device) race
+ * on it and must be serialised by the caller.  Nothing in the array needs
+ * clearing between calls: each call writes every part it reads.  Calls no
+ * cudaMalloc or cudaFree. */
 int  ts_residual_noalloc(ts_problem* prob, const float* y, float* r, void* stream);
+
+/* Assembled tangent of the paper's variant (section 2.5.2, eq. tangent and
+ * eq. K_mat with A and tau frozen at the state of the last ts_residual call,
+ * least-squares parts dropped from G_i and D_j, plus the pseudo-time mass of
+ * section 2.5.3 when dt_pseudo is finite), stored block by block as the paper
+ * describes: per connection of the node graph (nodes sharing an element, a
+ * node with itself included) the mode matrix K_AB, used for all three velocity
+ * fields, the mode matrix L_AB, and the six scalars of the mode-diagonal
+ * G_AB,i and D_AB,j: 2 (2N)^2 + 8 FP32 numbers, ts_assembled_bytes() in all.
+ * The blocks are those of TS_JVP_PAPER whatever the problem's variant.
+ * ts_assemble builds them on the device (library-owned memory, allocated at
+ * the first call); TS_ERR_ARG if no residual was computed yet,
+ * TS_ERR_UNSUPPORTED for a problem with backflow faces.  A later ts_residual
+ * invalidates them. */
+int  ts_assemble(ts_problem* prob, void* stream);
+/* Hv = H v with the assembled blocks, plus the resistance-outlet coupling
+ * (evaluated matrix-free, as in ts_jvp); FP32 fields in the layout above,
+ * caller-owned device memory.  Dirichlet velocity entries and Im(mode 0) of
+ * v are ignored and the same rows of Hv are zero.  Equals ts_jvp of a
+ * TS_JVP_PAPER problem at the same state.  TS_ERR_ARG before ts_assemble or
+ * when v and Hv alias. */
+int  ts_spmv(ts_problem* prob, const float* v, float* Hv, void* stream);
+/* bytes of the assembled blocks (or a negative error) */
+int64_t ts_assembled_bytes(const ts_problem* prob);
+/* connections of the node graph of a mesh (or a negative error) */
+int64_t ts_mesh_connections(const ts_mesh* mesh);
+
+/* Nodal diagonal blocks H_AA of the tangent (eq. tangent, eq. K_mat, with A and
+ * tau frozen at the state of the last ts_residual call, plus the pseudo-time
+ * mass of section 2.5.3 when dt_pseudo is finite and the resistance-outlet
+ * coupling of the node with itself): for every node A the 8N x 8N matrix that
+ * maps the node's own unknowns (field, mode, re/im in the layout above) to its
+ * own rows, summed over the elements around A.  K is shared by the three
+ * velocity fields; TS_JVP_PAPER drops the least-squares parts of G_i and D_j
+ * (section 2.5.2); a TS_JVP_LIN_A problem gets the blocks of TS_JVP_FROZEN
+ * (the derivative of A_j is left out).  These blocks are the preconditioner of
+ * ts_solve with precond = 2.
+ *   blocks  caller-owned FP32 device array [V][8N][8N]
+ *   invert  0: H_AA row-major (row = field * 2N + 2 mode + re/im), with the
+ *           rows and columns of fixed unknowns (Im(mode 0), Dirichlet
+ *           velocity) zero; 1: the inverse of H_AA with those rows and columns
+ *           replaced by the identity, stored COLUMN-major (the layout the
+ *           preconditioner reads).  Computed in FP32.
+ * TS_ERR_ARG if no residual was computed yet.  A block that cannot be inverted
+ * is stored as the identity. */
+int  ts_block_diagonal(ts_problem* prob, float* blocks, int invert, void* stream);
 
 /* Tangent product Hv (eq. K_mat, variant from the problem) at the state of
  * the last ts_residual call, plus c1 rho / dt_pseudo M v on the momentum rows

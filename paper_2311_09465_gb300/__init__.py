@@ -21,6 +21,8 @@ LIB_PATH = os.path.join(_HERE, "lib", "libtsgls.so")
 TS_OK, TS_ERR_ARG, TS_ERR_CUDA, TS_ERR_OOM, TS_ERR_NOCONV, TS_ERR_NAN, TS_ERR_UNSUPPORTED = (
     0, -1, -2, -3, -4, -5, -6)
 TS_BC_DIRICHLET, TS_BC_TRACTION, TS_BC_RESISTANCE, TS_BC_BACKFLOW = 1, 2, 3, 4
+TS_PROFILE_PARABOLIC, TS_PROFILE_WOMERSLEY = 1, 2
+PROFILES = {"parabolic": TS_PROFILE_PARABOLIC, "womersley": TS_PROFILE_WOMERSLEY}
 TS_JVP_PAPER, TS_JVP_FROZEN, TS_JVP_LIN_A = 0, 1, 2
 VARIANTS = {"paper": TS_JVP_PAPER, "frozen": TS_JVP_FROZEN, "lin_a": TS_JVP_LIN_A}
 TS_OPT_TAU64, TS_OPT_FP32_TANGENT = 1, 2
@@ -53,7 +55,8 @@ class ts_solve_report(ctypes.Structure):
                 ("r_final", ctypes.c_double), ("seconds", ctypes.c_double),
                 ("t_residual", ctypes.c_double), ("t_jvp", ctypes.c_double),
                 ("t_krylov", ctypes.c_double), ("hist_len", ctypes.c_int),
-                ("hist", ctypes.c_double * 512), ("rejected", ctypes.c_int)]
+                ("hist", ctypes.c_double * 512), ("rejected", ctypes.c_int),
+                ("t_precond", ctypes.c_double)]
 
     def to_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "hist"}
@@ -83,8 +86,18 @@ def lib() -> ctypes.CDLL:
     L.ts_problem_set.argtypes = [vp, ctypes.c_double, ctypes.c_int]
     L.ts_set_bc.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double]
     L.ts_problem_option.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    L.ts_set_inlet.argtypes = [vp, ctypes.c_int, dp, ctypes.c_int]
+    L.ts_inlet_info.argtypes = [vp, ctypes.c_int, dp]
+    L.ts_initial_guess.argtypes = [vp, vp, ctypes.c_int, vp]
     L.ts_residual.argtypes = [vp, vp, vp, ctypes.c_int, vp]
     L.ts_jvp.argtypes = [vp, vp, vp, ctypes.c_int, vp]
+    L.ts_block_diagonal.argtypes = [vp, vp, ctypes.c_int, vp]
+    L.ts_assemble.argtypes = [vp, vp]
+    L.ts_spmv.argtypes = [vp, vp, vp, vp]
+    L.ts_assembled_bytes.argtypes = [vp]
+    L.ts_assembled_bytes.restype = ctypes.c_int64
+    L.ts_mesh_connections.argtypes = [vp]
+    L.ts_mesh_connections.restype = ctypes.c_int64
     L.ts_residual_noalloc.argtypes = [vp, vp, vp, vp]
     L.ts_solve.argtypes = [vp, vp, ctypes.POINTER(ts_solve_opts), ctypes.POINTER(ts_solve_report), vp]
     fp, u64 = ctypes.POINTER(ctypes.c_float), ctypes.c_uint64
@@ -213,6 +226,26 @@ def ts_set_bc(prob, tag: int, kind: int, value: float = 0.0):
     _check(lib().ts_set_bc(prob, tag, kind, value))
 
 
+def ts_set_inlet(prob, tag: int, Qn, profile="parabolic"):
+    """Inlet Dirichlet data from complex flow-rate coefficients Qn (modes 0..N-1)."""
+    q = np.asarray(Qn, dtype=np.complex128)
+    buf = np.ascontiguousarray(np.stack([q.real, q.imag], axis=1), dtype=np.float64)
+    _check(lib().ts_set_inlet(prob, tag, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                              PROFILES[profile] if isinstance(profile, str) else int(profile)))
+
+
+def ts_inlet_info(prob, tag: int) -> dict:
+    out = np.zeros(7)
+    _check(lib().ts_inlet_info(prob, tag, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return {"centre": out[0:3].copy(), "direction": out[3:6].copy(), "radius": float(out[6])}
+
+
+def ts_initial_guess(prob, y, stream=None):
+    py, p = _field_ptr(y)
+    _check(lib().ts_initial_guess(prob, py, p, _stream_ptr(stream)))
+    return y
+
+
 def ts_residual(prob, y, r, precision=None, stream=None):
     py, p = _field_ptr(y, precision)
     pr, _ = _field_ptr(r, p)
@@ -233,6 +266,42 @@ def ts_jvp(prob, v, hv, precision=None, stream=None):
     ph, _ = _field_ptr(hv, p)
     _check(lib().ts_jvp(prob, pv, ph, p, _stream_ptr(stream)))
     return hv
+
+
+def ts_block_diagonal(prob, out, invert=False, stream=None):
+    """Nodal diagonal blocks of the tangent into out (CUDA float32 [V, 8N, 8N]);
+    invert: their inverses, column-major (see include/tsgls.h)."""
+    import torch
+    if not out.is_cuda or out.dtype != torch.float32 or not out.is_contiguous():
+        raise ValueError("out must be a contiguous CUDA float32 tensor")
+    _check(lib().ts_block_diagonal(prob, ctypes.c_void_p(out.data_ptr()), int(bool(invert)),
+                                   _stream_ptr(stream)))
+    return out
+
+
+def ts_assemble(prob, stream=None):
+    _check(lib().ts_assemble(prob, _stream_ptr(stream)))
+
+
+def ts_spmv(prob, v, hv, stream=None):
+    pv, _ = _field_ptr(v, 32)
+    ph, _ = _field_ptr(hv, 32)
+    _check(lib().ts_spmv(prob, pv, ph, _stream_ptr(stream)))
+    return hv
+
+
+def ts_assembled_bytes(prob) -> int:
+    n = int(lib().ts_assembled_bytes(prob))
+    if n < 0:
+        _check(n)
+    return n
+
+
+def ts_mesh_connections(mesh) -> int:
+    n = int(lib().ts_mesh_connections(mesh))
+    if n < 0:
+        _check(n)
+    return n
 
 
 def ts_solve(prob, y, opts: ts_solve_opts, stream=None, raise_on_noconv=True) -> dict:
@@ -277,6 +346,18 @@ class GLSProblem:
             ts_problem_option(self.prob, TS_OPT_FP32_TANGENT,
                               {"single": 0, "coloured": 1}[fp32_tangent])
 
+    def set_inlet(self, tag, Qn, profile="parabolic"):
+        ts_set_inlet(self.prob, tag, Qn, profile)
+
+    def inlet_info(self, tag):
+        return ts_inlet_info(self.prob, tag)
+
+    def initial_guess(self, dtype=None, stream=None):
+        """The paper's initial guess with the inlet data of set_inlet (new CUDA tensor)."""
+        import torch
+        y = self.field(torch.float64 if dtype is None else dtype)
+        return ts_initial_guess(self.prob, y, stream)
+
     def set(self, dt_pseudo=math.inf, variant="lin_a"):
         ts_problem_set(self.prob, dt_pseudo, VARIANTS[variant])
 
@@ -294,6 +375,22 @@ class GLSProblem:
     def jvp(self, v, hv=None, stream=None):
         hv = self.field(v.dtype, v.device) if hv is None else hv
         return ts_jvp(self.prob, v, hv, stream=stream)
+
+    def assemble(self, stream=None):
+        ts_assemble(self.prob, stream)
+
+    def spmv(self, v, hv=None, stream=None):
+        hv = self.field(v.dtype, v.device) if hv is None else hv
+        return ts_spmv(self.prob, v, hv, stream)
+
+    def assembled_bytes(self):
+        return ts_assembled_bytes(self.prob)
+
+    def block_diagonal(self, invert=False, stream=None):
+        import torch
+        nb = 8 * self.N
+        out = torch.empty((self.n_nodes, nb, nb), dtype=torch.float32, device="cuda")
+        return ts_block_diagonal(self.prob, out, invert, stream)
 
     def solve(self, y, precision=64, tol=1e-8, r_ref=0.0, max_steps=200, krylov=100,
               eps_ls=0.05, max_matvec=10000, verbose=False, stream=None, raise_on_noconv=True,

@@ -2,11 +2,14 @@
 // residual and tangent dispatch, and the pseudo-time Newton-GMRES solve
 // (sections 2.4-2.5 of Esmaily & Jia, arXiv 2311.09465).
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <complex>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -26,6 +29,10 @@ int fail(int code, const std::string& msg) {
 }  // namespace ts
 
 namespace {
+
+// loads the allocation-free residual's arrays and kernels on the current
+// device (defined with that entry point below)
+int noalloc_setup(int N);
 
 bool n_supported(int N) {
   const int list[] = {TS_N_LIST};
@@ -47,6 +54,13 @@ struct ts_mesh {
   int4* d_tets = nullptr;
   double* d_geo64 = nullptr;
   float* d_geo32 = nullptr;
+  int32_t* d_node_off = nullptr;      // [V + 1] node-to-element list offsets
+  int32_t* d_node_elem = nullptr;     // [4E] element * 4 + local node (colour-sorted ids)
+  int64_t nnzb = 0;                   // node-graph connections (A itself included)
+  int32_t* d_row_off = nullptr;       // [V + 1] node graph in CSR
+  int32_t* d_cols = nullptr;          // [nnzb] sorted neighbour ids per row
+  std::vector<int64_t> ncolour_off;   // node colouring of the node graph: colour c holds
+  int32_t* d_node_perm = nullptr;     // d_node_perm[ncolour_off[c] .. ncolour_off[c+1])
 };
 
 template <typename T>
@@ -72,6 +86,17 @@ struct Outlet {
   float* d_w32 = nullptr;
 };
 
+// inflow boundary data of one inlet tag (section 2.4, eq. upgh_def)
+struct Inlet {
+  int tag = 0;
+  int profile = 0;
+  double centre[3] = {0, 0, 0}, dir[3] = {0, 0, 0}, R = 0;   // dir: unit inflow direction
+  std::vector<int32_t> nodes;   // every node of the tag (rim nodes get zero velocity)
+  std::vector<double> vals;     // [n][3][C] Dirichlet velocity modes
+  int32_t* d_nodes = nullptr;
+  double* d_vals = nullptr;
+};
+
 struct BackflowSet {
   int tag;
   double beta;
@@ -91,6 +116,7 @@ struct ts_problem {
   bool dmask_dirty = true;
   std::vector<Outlet> outlets;
   std::vector<BackflowSet> backflow;
+  std::vector<Inlet> inlets;
   int64_t bf_points = 0;         // 3 per backflow face
   LinState<float> l32;
   LinState<double> l64;
@@ -101,6 +127,12 @@ struct ts_problem {
   double *d_w = nullptr, *d_r = nullptr, *d_dy = nullptr, *d_partial = nullptr, *d_h = nullptr;
   float *d_v32 = nullptr, *d_w32 = nullptr;
   double *d_D = nullptr, *d_t = nullptr;      // preconditioner diagonal (inverted), temp
+  float* d_binv = nullptr;                    // inverted nodal blocks [V][8N][8N] (block Jacobi)
+  float* d_hasm = nullptr;                    // assembled PAPER tangent records [nnzb][2C^2 + 8]
+  float *d_r32 = nullptr, *d_z32 = nullptr;   // block Gauss-Seidel work vectors
+  bool hasm_valid = false;
+  float* d_outdiag = nullptr;                 // [V][6] outlet R w_i w_j per node
+  bool outdiag_dirty = true;
   cudaEvent_t ev_a = nullptr, ev_b = nullptr; // time of the tangent products in a solve
   // stage times (ts_stage_times): tau start/end and element pass end of the
   // last residual; element kernel start/end of the last FP32 tangent product
@@ -334,6 +366,7 @@ static int residual_impl(ts_problem* pr, const T* y, T* r, cudaStream_t st) {
       return fail(TS_ERR_CUDA, "node sample kernel failed");
   }
   l.valid = true;
+  pr->hasm_valid = false;
   // the other precision's state is now stale
   if (sizeof(T) == 4) pr->l64.valid = false; else pr->l32.valid = false;
   return 0;
@@ -478,6 +511,149 @@ static int precond_diag(ts_problem* pr, const double* y, double* D, cudaStream_t
       return fail(TS_ERR_CUDA, "diag kernel");
   if (launch_diag_invert(D, pr->d_dmask, msh->V, pr->C, st)) return fail(TS_ERR_CUDA, "diag invert");
   return 0;
+}
+
+// per-node outlet couplings R w_i w_j (the diagonal part of the resistance term)
+static int sync_outdiag(ts_problem* pr) {
+  if (!pr->d_outdiag) TS_TRY(dalloc(&pr->d_outdiag, (size_t)pr->mesh->V * 6));
+  if (!pr->outdiag_dirty) return 0;
+  std::vector<float> od((size_t)pr->mesh->V * 6, 0.f);
+  for (auto& o : pr->outlets)
+    for (size_t k = 0; k < o.nodes.size(); ++k) {
+      const double* w = &o.w[3 * k];
+      float* d = &od[(size_t)o.nodes[k] * 6];
+      d[0] += (float)(o.R * w[0] * w[0]);
+      d[1] += (float)(o.R * w[0] * w[1]);
+      d[2] += (float)(o.R * w[0] * w[2]);
+      d[3] += (float)(o.R * w[1] * w[1]);
+      d[4] += (float)(o.R * w[1] * w[2]);
+      d[5] += (float)(o.R * w[2] * w[2]);
+    }
+  TS_CUDA(cudaMemcpy(pr->d_outdiag, od.data(), od.size() * 4, cudaMemcpyHostToDevice));
+  pr->outdiag_dirty = false;
+  return 0;
+}
+
+template <typename T, int N>
+static int block_diag_impl(ts_problem* pr, LinState<T>& l, int invert, float* out, cudaStream_t st) {
+  const ts_mesh* m = pr->mesh;
+  Phys<double> p64 = phys_of<double>(pr, true);
+  Phys<float> ph{(float)p64.rho, (float)p64.mu, (float)p64.omega, (float)p64.nu, (float)p64.C_I,
+                 (float)p64.mass_coef};
+  const int paper = pr->p.jvp_variant == TS_JVP_PAPER;
+  int rc = launch_block_diag<T, N>(paper, invert, m->d_node_off, m->d_node_elem, m->d_tets, geo_of<T>(m),
+                                   l.u0, l.tau, pr->d_dmask, pr->d_outdiag, ph, out, m->V, pr->d_counter, st);
+  if (rc) return fail(rc == -6 ? TS_ERR_UNSUPPORTED : TS_ERR_CUDA, "block diagonal kernel launch failed");
+  return 0;
+}
+
+// nodal diagonal blocks of the tangent at the last residual's state
+static int block_diag_any(ts_problem* pr, int invert, float* out, cudaStream_t st) {
+  TS_TRY(sync_dmask(pr));
+  TS_TRY(sync_outdiag(pr));
+  if (pr->l64.valid) {
+    TS_DISPATCH(pr->p.N, (block_diag_impl<double, NN>(pr, pr->l64, invert, out, st)));
+  }
+  if (pr->l32.valid) {
+    TS_DISPATCH(pr->p.N, (block_diag_impl<float, NN>(pr, pr->l32, invert, out, st)));
+  }
+  return fail(TS_ERR_ARG, "block diagonal: no linearisation state (call ts_residual first)");
+}
+
+static int block_apply_any(ts_problem* pr, const double* x, double* z, cudaStream_t st) {
+  int rc = 0;
+  switch (pr->p.N) {
+#define TS_BAPPLY_CASE(NV) case NV: rc = launch_block_apply<NV>(pr->d_binv, x, z, pr->mesh->V, st); break;
+    TS_BAPPLY_CASE(1) TS_BAPPLY_CASE(2) TS_BAPPLY_CASE(3) TS_BAPPLY_CASE(4) TS_BAPPLY_CASE(5)
+    TS_BAPPLY_CASE(7) TS_BAPPLY_CASE(10) TS_BAPPLY_CASE(15)
+#undef TS_BAPPLY_CASE
+    default: return fail(TS_ERR_UNSUPPORTED, "no kernel compiled for this N");
+  }
+  return rc ? fail(TS_ERR_CUDA, "block apply kernel launch failed") : 0;
+}
+
+static int block_precond_setup(ts_problem* pr, cudaStream_t st) {
+  const int64_t nb = 8 * (int64_t)pr->p.N;
+  if (!pr->d_binv) TS_TRY(dalloc(&pr->d_binv, (size_t)pr->mesh->V * nb * nb));
+  return block_diag_any(pr, 1, pr->d_binv, st);
+}
+
+template <typename T, int N>
+static int assemble_impl(ts_problem* pr, LinState<T>& l, cudaStream_t st) {
+  const ts_mesh* m = pr->mesh;
+  if (!pr->d_hasm) TS_TRY(dalloc(&pr->d_hasm, (size_t)m->nnzb * assembled_record_floats(N)));
+  Phys<double> p64 = phys_of<double>(pr, true);
+  Phys<float> ph{(float)p64.rho, (float)p64.mu, (float)p64.omega, (float)p64.nu, (float)p64.C_I,
+                 (float)p64.mass_coef};
+  int rc = launch_assemble_paper<T, N>(m->d_node_off, m->d_node_elem, m->d_row_off, m->d_cols, m->d_tets,
+                                       geo_of<T>(m), l.u0, l.tau, ph, pr->d_hasm, m->V, st);
+  if (rc) return fail(rc == -6 ? TS_ERR_UNSUPPORTED : TS_ERR_CUDA, "assembly kernel launch failed");
+  pr->hasm_valid = true;
+  return 0;
+}
+
+static int assemble_any(ts_problem* pr, cudaStream_t st) {
+  if (!pr->backflow.empty()) return fail(TS_ERR_UNSUPPORTED, "assembled tangent: backflow faces not supported");
+  if (pr->l64.valid) {
+    TS_DISPATCH(pr->p.N, (assemble_impl<double, NN>(pr, pr->l64, st)));
+  }
+  if (pr->l32.valid) {
+    TS_DISPATCH(pr->p.N, (assemble_impl<float, NN>(pr, pr->l32, st)));
+  }
+  return fail(TS_ERR_ARG, "assembled tangent: no linearisation state (call ts_residual first)");
+}
+
+template <int N>
+static int spmv_impl(ts_problem* pr, const float* v, float* hv, cudaStream_t st) {
+  const ts_mesh* m = pr->mesh;
+  int rc = launch_spmv_paper<N>(m->d_row_off, m->d_cols, pr->d_hasm, pr->d_dmask, v, hv, m->V, st);
+  if (rc) return fail(rc == -6 ? TS_ERR_UNSUPPORTED : TS_ERR_CUDA, "assembled product kernel launch failed");
+  for (auto& o : pr->outlets)
+    if (launch_outlet<float>(o.d_nodes, outlet_w<float>(o), (int)o.nodes.size(), (float)o.R, v, pr->d_dmask, 1,
+                             hv, pr->C, st))
+      return fail(TS_ERR_CUDA, "outlet kernel launch failed");
+  return 0;
+}
+
+static int spmv_any(ts_problem* pr, const float* v, float* hv, cudaStream_t st) {
+  if (!pr->hasm_valid) return fail(TS_ERR_ARG, "ts_spmv: no assembled tangent (call ts_assemble first)");
+  TS_DISPATCH(pr->p.N, (spmv_impl<NN>(pr, v, hv, st)));
+}
+
+// Symmetric block Gauss-Seidel with the assembled records (precond 3): a
+// forward sweep over the node colours from z = 0, then a backward sweep
+template <int N>
+static int sgs_impl(ts_problem* pr, cudaStream_t st) {
+  const ts_mesh* m = pr->mesh;
+  const int nc = (int)m->ncolour_off.size() - 1;
+  for (int pass = 0; pass < 2; ++pass)
+    for (int k = 0; k < nc; ++k) {
+      const int c = pass == 0 ? k : nc - 1 - k;
+      const int64_t o0 = m->ncolour_off[c], o1 = m->ncolour_off[c + 1];
+      if (launch_sgs_colour<N>(m->d_node_perm + o0, o1 - o0, m->d_row_off, m->d_cols, pr->d_hasm, pr->d_binv,
+                               pr->d_dmask, pr->d_r32, pr->d_z32, st))
+        return fail(TS_ERR_CUDA, "block Gauss-Seidel kernel launch failed");
+    }
+  return 0;
+}
+
+static int sgs_apply_any(ts_problem* pr, const double* x, double* z, cudaStream_t st) {
+  const int64_t n = field_len(pr);
+  if (vec_cast_d2f(pr->d_r32, x, n, st)) return fail(TS_ERR_CUDA, "cast");
+  TS_CUDA(cudaMemsetAsync(pr->d_z32, 0, n * sizeof(float), st));
+  TS_DISPATCH(pr->p.N, ([&]() -> int {
+    TS_TRY(sgs_impl<NN>(pr, st));
+    if (vec_cast_f2d(z, pr->d_z32, n, st)) return fail(TS_ERR_CUDA, "cast");
+    return 0;
+  }()));
+}
+
+static int sgs_setup(ts_problem* pr, cudaStream_t st) {
+  const int64_t n = field_len(pr);
+  if (!pr->d_r32) TS_TRY(dalloc(&pr->d_r32, (size_t)n));
+  if (!pr->d_z32) TS_TRY(dalloc(&pr->d_z32, (size_t)n));
+  TS_TRY(block_precond_setup(pr, st));
+  return assemble_any(pr, st);
 }
 
 namespace ts {
@@ -661,13 +837,73 @@ int ts_mesh_load(const double* xyz_host, int64_t n_nodes, const int32_t* tets_ho
     m->bfaces[3 * f + 2] = c;
   }
   std::vector<float> geo32(geo.begin(), geo.end());
+  // node-to-element list over the colour-sorted elements (element * 4 + local node)
+  std::vector<int32_t> noff(n_nodes + 1, 0), nel(4 * n_tets);
+  for (int64_t i = 0; i < 4 * n_tets; ++i) noff[m->tets[i] + 1]++;
+  for (int64_t v = 0; v < n_nodes; ++v) noff[v + 1] += noff[v];
+  {
+    std::vector<int32_t> fill(noff.begin(), noff.end() - 1);
+    for (int64_t d = 0; d < n_tets; ++d)
+      for (int a = 0; a < 4; ++a) nel[fill[m->tets[4 * d + a]]++] = (int32_t)(4 * d + a);
+  }
+  // node graph (nodes sharing an element, the node itself included), sorted rows
+  std::vector<int32_t> roff(n_nodes + 1, 0), cols;
+  {
+    std::vector<int32_t> nb;
+    for (int64_t v = 0; v < n_nodes; ++v) {
+      nb.clear();
+      for (int32_t p = noff[v]; p < noff[v + 1]; ++p) {
+        const int32_t d = nel[p] >> 2;
+        for (int a = 0; a < 4; ++a) nb.push_back(m->tets[4 * (int64_t)d + a]);
+      }
+      std::sort(nb.begin(), nb.end());
+      nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
+      cols.insert(cols.end(), nb.begin(), nb.end());
+      roff[v + 1] = (int32_t)cols.size();
+    }
+  }
+  m->nnzb = (int64_t)cols.size();
+  // greedy colouring of the node graph: no two nodes of a colour share an element
+  std::vector<int32_t> ncl(n_nodes, -1), perm(n_nodes);
+  {
+    std::vector<int64_t> mark;
+    int nc = 0;
+    for (int64_t v = 0; v < n_nodes; ++v) {
+      mark.assign(nc + 1, -1);
+      for (int32_t p = roff[v]; p < roff[v + 1]; ++p)
+        if (ncl[cols[p]] >= 0) mark[ncl[cols[p]]] = v;
+      int c = 0;
+      while (c < nc && mark[c] == v) ++c;
+      ncl[v] = c;
+      if (c == nc) ++nc;
+    }
+    std::vector<int64_t> cnt(nc + 1, 0);
+    for (int64_t v = 0; v < n_nodes; ++v) cnt[ncl[v] + 1]++;
+    for (int c = 0; c < nc; ++c) cnt[c + 1] += cnt[c];
+    m->ncolour_off = cnt;
+    std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+    for (int64_t v = 0; v < n_nodes; ++v) perm[fill[ncl[v]]++] = (int32_t)v;
+  }
   int rc = 0;
   rc |= dalloc(&m->d_tets, (size_t)n_tets);
   rc |= dalloc(&m->d_geo64, geo.size());
   rc |= dalloc(&m->d_geo32, geo32.size());
+  rc |= dalloc(&m->d_node_off, noff.size());
+  rc |= dalloc(&m->d_node_elem, nel.size());
+  rc |= dalloc(&m->d_row_off, roff.size());
+  rc |= dalloc(&m->d_cols, cols.size());
+  rc |= dalloc(&m->d_node_perm, perm.size());
   if (rc) {
     ts_mesh_free(m);
     return TS_ERR_OOM;
+  }
+  if (cudaMemcpy(m->d_node_off, noff.data(), noff.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(m->d_node_elem, nel.data(), nel.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(m->d_row_off, roff.data(), roff.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(m->d_cols, cols.data(), cols.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(m->d_node_perm, perm.data(), perm.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+    ts_mesh_free(m);
+    return fail(TS_ERR_CUDA, "ts_mesh_load: host-to-device copy failed");
   }
   cudaError_t e1 = cudaMemcpy(m->d_tets, m->tets.data(), 16 * n_tets, cudaMemcpyHostToDevice);
   cudaError_t e2 = cudaMemcpy(m->d_geo64, geo.data(), geo.size() * 8, cudaMemcpyHostToDevice);
@@ -685,6 +921,11 @@ void ts_mesh_free(ts_mesh* m) {
   dfree(m->d_tets);
   dfree(m->d_geo64);
   dfree(m->d_geo32);
+  dfree(m->d_node_off);
+  dfree(m->d_node_elem);
+  dfree(m->d_row_off);
+  dfree(m->d_cols);
+  dfree(m->d_node_perm);
   delete m;
 }
 
@@ -720,6 +961,11 @@ int ts_problem_create(const ts_mesh* mesh, const ts_params* params, ts_problem**
     return TS_ERR_OOM;
   }
   cudaMemset(pr->d_counter, 0, sizeof(unsigned));
+  // the allocation-free residual must not load anything at call time
+  if (int rc = noalloc_setup(p.N)) {
+    ts_problem_free(pr);
+    return rc;
+  }
   *out = pr;
   return 0;
 }
@@ -736,6 +982,10 @@ void ts_problem_free(ts_problem* pr) {
     dfree(o.d_nodes);
     dfree(o.d_w64);
     dfree(o.d_w32);
+  }
+  for (auto& in : pr->inlets) {
+    dfree(in.d_nodes);
+    dfree(in.d_vals);
   }
   for (auto& b : pr->backflow) {
     dfree(b.d_faces);
@@ -756,6 +1006,11 @@ void ts_problem_free(ts_problem* pr) {
   dfree(pr->d_w32);
   dfree(pr->d_D);
   dfree(pr->d_t);
+  dfree(pr->d_binv);
+  dfree(pr->d_hasm);
+  dfree(pr->d_r32);
+  dfree(pr->d_z32);
+  dfree(pr->d_outdiag);
   delete pr;
 }
 
@@ -781,6 +1036,202 @@ int ts_problem_option(ts_problem* pr, int key, int value) {
     return 0;
   }
   return fail(TS_ERR_ARG, "unknown option key");
+}
+
+}  // extern "C"
+
+namespace {
+
+// J_nu(z), nu = 0 or 1, from its power series sum_k (-1)^k (z/2)^(2k+nu) / (k! (k+nu)!)
+// (Abramowitz & Stegun 9.1.10); adequate for |z| up to about 30
+std::complex<double> bessel_j_series(int nu, std::complex<double> z) {
+  const std::complex<double> h = 0.5 * z, h2 = h * h;
+  std::complex<double> term = nu == 0 ? std::complex<double>(1.0) : h;
+  std::complex<double> sum = term;
+  for (int k = 1; k < 400; ++k) {
+    term *= -h2 / (double)(k * (k + nu));
+    sum += term;
+    if (std::abs(term) <= 1e-18 * std::abs(sum) && k > std::abs(h) + 2) break;
+  }
+  return sum;
+}
+
+// velocity mode n at radius r of a profile with flow-rate coefficient Q and mean
+// velocity U = Q / (pi R^2): parabolic 2U(1 - r^2/R^2), or the Womersley mode
+// U [1 - J0(L r/R) / J0(L)] / [1 - 2 J1(L) / (L J0(L))], L = i^{3/2} alpha_n,
+// alpha_n = R sqrt(n omega / nu) (mode 0 of Womersley is the parabola)
+std::complex<double> inlet_mode_value(int profile, int n, double r, double R, std::complex<double> Q,
+                                      double omega, double nu) {
+  const double pi = 3.14159265358979323846;
+  const std::complex<double> U = Q / (pi * R * R);
+  const double x = std::min(r / R, 1.0);
+  if (profile == TS_PROFILE_PARABOLIC || n == 0) return 2.0 * U * (1.0 - x * x);
+  const double alpha = R * std::sqrt(n * omega / nu);
+  const std::complex<double> i32 = std::polar(1.0, 0.75 * pi);   // i^{3/2}
+  const std::complex<double> L = i32 * alpha;
+  const std::complex<double> j0 = bessel_j_series(0, L);
+  const std::complex<double> shape = 1.0 - bessel_j_series(0, L * x) / j0;
+  const std::complex<double> mean_shape = 1.0 - 2.0 * bessel_j_series(1, L) / (L * j0);
+  return U * shape / mean_shape;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ts_set_inlet(ts_problem* pr, int tag, const double* Qn_host, int profile) {
+  if (!pr || !Qn_host) return fail(TS_ERR_ARG, "ts_set_inlet: NULL argument");
+  if (profile != TS_PROFILE_PARABOLIC && profile != TS_PROFILE_WOMERSLEY)
+    return fail(TS_ERR_ARG, "ts_set_inlet: unknown profile");
+  const ts_mesh* m = pr->mesh;
+  const int N = pr->p.N, C = pr->C;
+  for (int n = 0; n < N; ++n)
+    if (!std::isfinite(Qn_host[2 * n]) || !std::isfinite(Qn_host[2 * n + 1]))
+      return fail(TS_ERR_ARG, "ts_set_inlet: non-finite flow-rate coefficient");
+  // outward normal (faces are oriented outward at ts_mesh_load), tag nodes, rim nodes
+  double nrm[3] = {0, 0, 0};
+  std::vector<uint8_t> on_tag(m->V, 0), on_other(m->V, 0);
+  for (int64_t f = 0; f < m->F; ++f) {
+    const int32_t* t = &m->bfaces[3 * f];
+    if (m->btag[f] != tag) {
+      for (int k = 0; k < 3; ++k) on_other[t[k]] = 1;
+      continue;
+    }
+    const double* pa = &m->xyz[3 * t[0]];
+    double u[3], v[3];
+    for (int i = 0; i < 3; ++i) {
+      u[i] = m->xyz[3 * t[1] + i] - pa[i];
+      v[i] = m->xyz[3 * t[2] + i] - pa[i];
+    }
+    nrm[0] += u[1] * v[2] - u[2] * v[1];
+    nrm[1] += u[2] * v[0] - u[0] * v[2];
+    nrm[2] += u[0] * v[1] - u[1] * v[0];
+    for (int k = 0; k < 3; ++k) on_tag[t[k]] = 1;
+  }
+  const double nl = std::sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
+  if (!(nl > 0)) return fail(TS_ERR_ARG, "ts_set_inlet: no boundary face carries this tag");
+  Inlet in;
+  in.tag = tag;
+  in.profile = profile;
+  for (int i = 0; i < 3; ++i) in.dir[i] = -nrm[i] / nl;
+  // orthonormal in-plane basis e1, e2
+  const double* d = in.dir;
+  double e1[3];
+  if (std::fabs(d[0]) < 0.9) { e1[0] = 0; e1[1] = -d[2]; e1[2] = d[1]; }
+  else { e1[0] = d[2]; e1[1] = 0; e1[2] = -d[0]; }
+  const double l1 = std::sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
+  for (double& x : e1) x /= l1;
+  const double e2[3] = {d[1] * e1[2] - d[2] * e1[1], d[2] * e1[0] - d[0] * e1[2], d[0] * e1[1] - d[1] * e1[0]};
+  // circle through the rim nodes (algebraic least-squares fit, Kasa 1976):
+  // minimise sum (a^2 + b^2 + D a + E b + F)^2 over the in-plane coordinates (a, b)
+  double S[3][3] = {{0}}, rhs[3] = {0, 0, 0}, zsum = 0;
+  int n_rim = 0;
+  for (int64_t v = 0; v < m->V; ++v) {
+    if (!on_tag[v]) continue;
+    in.nodes.push_back((int32_t)v);
+    if (!on_other[v]) continue;
+    const double* x = &m->xyz[3 * v];
+    const double a = x[0] * e1[0] + x[1] * e1[1] + x[2] * e1[2];
+    const double b = x[0] * e2[0] + x[1] * e2[1] + x[2] * e2[2];
+    zsum += x[0] * d[0] + x[1] * d[1] + x[2] * d[2];
+    const double row[3] = {a, b, 1.0}, z = -(a * a + b * b);
+    for (int i = 0; i < 3; ++i) {
+      rhs[i] += row[i] * z;
+      for (int j = 0; j < 3; ++j) S[i][j] += row[i] * row[j];
+    }
+    ++n_rim;
+  }
+  if (n_rim < 3) return fail(TS_ERR_ARG, "ts_set_inlet: the tag's rim (nodes shared with other tags) has < 3 nodes");
+  // 3x3 solve by Cramer's rule
+  auto det3 = [](double A[3][3]) {
+    return A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+           A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+  };
+  const double dS = det3(S);
+  if (!(std::fabs(dS) > 0)) return fail(TS_ERR_ARG, "ts_set_inlet: degenerate inlet rim");
+  double sol[3];
+  for (int c = 0; c < 3; ++c) {
+    double T[3][3];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) T[i][j] = j == c ? rhs[i] : S[i][j];
+    sol[c] = det3(T) / dS;
+  }
+  const double ca = -0.5 * sol[0], cb = -0.5 * sol[1];
+  const double R2 = ca * ca + cb * cb - sol[2];
+  if (!(R2 > 0)) return fail(TS_ERR_ARG, "ts_set_inlet: inlet rim is not a circle");
+  in.R = std::sqrt(R2);
+  const double zc = zsum / n_rim;
+  for (int i = 0; i < 3; ++i) in.centre[i] = ca * e1[i] + cb * e2[i] + zc * d[i];
+  // Dirichlet velocity modes: profile x flow-rate coefficient along the inflow direction
+  const double nu = pr->p.mu / pr->p.rho;
+  in.vals.assign(in.nodes.size() * 3 * C, 0.0);
+  for (size_t k = 0; k < in.nodes.size(); ++k) {
+    const int32_t v = in.nodes[k];
+    if (on_other[v]) continue;   // the rim belongs to the wall: no-slip
+    const double* x = &m->xyz[3 * v];
+    double rel[3], ax = 0;
+    for (int i = 0; i < 3; ++i) rel[i] = x[i] - in.centre[i];
+    for (int i = 0; i < 3; ++i) ax += rel[i] * d[i];
+    double r2 = 0;
+    for (int i = 0; i < 3; ++i) {
+      const double pi_ = rel[i] - ax * d[i];
+      r2 += pi_ * pi_;
+    }
+    const double r = std::sqrt(r2);
+    for (int n = 0; n < N; ++n) {
+      const std::complex<double> Q(Qn_host[2 * n], n == 0 ? 0.0 : Qn_host[2 * n + 1]);
+      const std::complex<double> w = inlet_mode_value(profile, n, r, in.R, Q, pr->p.omega, nu);
+      for (int i = 0; i < 3; ++i) {
+        in.vals[(k * 3 + i) * C + 2 * n] = w.real() * d[i];
+        in.vals[(k * 3 + i) * C + 2 * n + 1] = n == 0 ? 0.0 : w.imag() * d[i];
+      }
+    }
+  }
+  for (int32_t v : in.nodes) pr->dmask[v] = 1;
+  pr->dmask_dirty = true;
+  TS_TRY(dalloc(&in.d_nodes, in.nodes.size()));
+  TS_TRY(dalloc(&in.d_vals, in.vals.size()));
+  TS_CUDA(cudaMemcpy(in.d_nodes, in.nodes.data(), in.nodes.size() * 4, cudaMemcpyHostToDevice));
+  TS_CUDA(cudaMemcpy(in.d_vals, in.vals.data(), in.vals.size() * 8, cudaMemcpyHostToDevice));
+  // a second call for the same tag replaces the first
+  for (auto it = pr->inlets.begin(); it != pr->inlets.end(); ++it)
+    if (it->tag == tag) {
+      dfree(it->d_nodes);
+      dfree(it->d_vals);
+      pr->inlets.erase(it);
+      break;
+    }
+  pr->inlets.push_back(std::move(in));
+  return 0;
+}
+
+int ts_inlet_info(const ts_problem* pr, int tag, double* out_host) {
+  if (!pr || !out_host) return fail(TS_ERR_ARG, "ts_inlet_info: NULL argument");
+  for (const auto& in : pr->inlets)
+    if (in.tag == tag) {
+      for (int i = 0; i < 3; ++i) {
+        out_host[i] = in.centre[i];
+        out_host[3 + i] = in.dir[i];
+      }
+      out_host[6] = in.R;
+      return 0;
+    }
+  return fail(TS_ERR_ARG, "ts_inlet_info: no inlet with this tag");
+}
+
+int ts_initial_guess(ts_problem* pr, void* y, int precision, void* stream) {
+  if (!pr || !y) return fail(TS_ERR_ARG, "ts_initial_guess: NULL argument");
+  if (precision != 32 && precision != 64) return fail(TS_ERR_ARG, "precision must be 32 or 64");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t esz = precision == 64 ? 8 : 4;
+  TS_CUDA(cudaMemsetAsync(y, 0, (size_t)field_len(pr) * esz, st));
+  for (const auto& in : pr->inlets) {
+    const int rc = precision == 64
+                       ? launch_inlet_fill<double>(in.d_nodes, in.d_vals, (int64_t)in.nodes.size(), pr->C, (double*)y, st)
+                       : launch_inlet_fill<float>(in.d_nodes, in.d_vals, (int64_t)in.nodes.size(), pr->C, (float*)y, st);
+    if (rc) return fail(TS_ERR_CUDA, "inlet fill kernel launch failed");
+  }
+  return 0;
 }
 
 int ts_set_bc(ts_problem* pr, int tag, int kind, double value) {
@@ -875,6 +1326,7 @@ int ts_set_bc(ts_problem* pr, int tag, int kind, double value) {
   TS_CUDA(cudaMemcpy(o.d_w64, o.w.data(), o.w.size() * 8, cudaMemcpyHostToDevice));
   TS_CUDA(cudaMemcpy(o.d_w32, w32.data(), w32.size() * 4, cudaMemcpyHostToDevice));
   pr->outlets.push_back(std::move(o));
+  pr->outdiag_dirty = true;
   return 0;
 }
 
@@ -884,6 +1336,35 @@ int ts_residual(ts_problem* pr, const void* y, void* r, int precision, void* str
   if (y == r) return fail(TS_ERR_ARG, "ts_residual: y and r alias");
   TS_TRY(sync_dmask(pr));
   return residual_any(pr, y, r, precision, (cudaStream_t)stream);
+}
+
+int ts_assemble(ts_problem* pr, void* stream) {
+  if (!pr) return fail(TS_ERR_ARG, "ts_assemble: NULL problem");
+  TS_TRY(sync_dmask(pr));
+  return assemble_any(pr, (cudaStream_t)stream);
+}
+
+int ts_spmv(ts_problem* pr, const float* v, float* hv, void* stream) {
+  if (!pr || !v || !hv) return fail(TS_ERR_ARG, "ts_spmv: NULL argument");
+  if ((const void*)v == (const void*)hv) return fail(TS_ERR_ARG, "ts_spmv: v and Hv alias");
+  TS_TRY(sync_dmask(pr));
+  return spmv_any(pr, v, hv, (cudaStream_t)stream);
+}
+
+int64_t ts_assembled_bytes(const ts_problem* pr) {
+  if (!pr) return fail(TS_ERR_ARG, "ts_assembled_bytes: NULL problem");
+  return pr->mesh->nnzb * (int64_t)assembled_record_floats(pr->p.N) * 4;
+}
+
+int64_t ts_mesh_connections(const ts_mesh* m) {
+  if (!m) return fail(TS_ERR_ARG, "ts_mesh_connections: NULL mesh");
+  return m->nnzb;
+}
+
+int ts_block_diagonal(ts_problem* pr, float* blocks, int invert, void* stream) {
+  if (!pr || !blocks) return fail(TS_ERR_ARG, "ts_block_diagonal: NULL argument");
+  if (invert != 0 && invert != 1) return fail(TS_ERR_ARG, "ts_block_diagonal: invert must be 0 or 1");
+  return block_diag_any(pr, invert, blocks, (cudaStream_t)stream);
 }
 
 int ts_jvp(ts_problem* pr, const void* v, void* hv, int precision, void* stream) {
@@ -899,71 +1380,105 @@ int ts_jvp(ts_problem* pr, const void* v, void* hv, int precision, void* stream)
 // ------------------------------------------------------------------ allocation-free residual
 // For callers that must not allocate device memory at call time (for example
 // code running inside a real-time loop or under an allocator that forbids
-// new device allocations): the FP32 residual with tau, tau L and the DFT
-// tables held in one file-scope device array instead of the problem's
-// lazily allocated buffers.  The array is created when a device loads this
-// library and lives until the process exits.
+// new device allocations): the FP32 residual with tau and tau L held in one
+// file-scope device array and the DFT tables in a second, small one, instead
+// of the problem's lazily allocated buffers.  Both arrays belong to this
+// translation unit's module; ts_problem_create loads that module on the
+// current device (looking up the arrays' addresses forces it, also under
+// CUDA's lazy module loading), fills the tables once per device and loads the
+// two kernels the entry point launches, so the entry point itself only
+// launches kernels and clears r.
 namespace {
 
 constexpr size_t kNoAllocFloats = (32u << 20) / sizeof(float);   // 32 MiB per device
 static __device__ __align__(256) float g_noalloc_scratch[kNoAllocFloats];
-float* g_noalloc_ptr[64] = {nullptr};
 
-// Device address of the scratch array for the current device, looked up once
-// per device with that device current.
-int noalloc_scratch(float** out) {
+constexpr int dft_total_floats() {
+  const int list[] = {TS_N_LIST};
+  int off = 0;
+  for (int n : list) off += 2 * (3 * n - 2) * (2 * n);
+  return off;
+}
+// FP32 DFT tables of every compiled N, each at dft_constant_offset(N)
+static __device__ __align__(16) float g_noalloc_dft[dft_total_floats()];
+
+constexpr int kMaxDevices = 64;
+struct NoAllocDevice {
+  std::atomic<float*> scratch{nullptr};
+  std::atomic<float*> dft{nullptr};
+};
+NoAllocDevice g_noalloc[kMaxDevices];
+std::mutex g_noalloc_mutex;
+
+// Device addresses of the two arrays for the current device; the first call
+// on a device (made by ts_problem_create) resolves them with that device
+// current and uploads the tables.
+int noalloc_arrays(float** scratch, float** dft) {
   int dev = 0;
   TS_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) return fail(TS_ERR_ARG, "ts_residual_noalloc: device index >= 64");
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    TS_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-    g_noalloc_ptr[dev] = static_cast<float*>(p);
+  if (dev < 0 || dev >= kMaxDevices) return fail(TS_ERR_ARG, "allocation-free residual: device index >= 64");
+  NoAllocDevice& d = g_noalloc[dev];
+  float* s = d.scratch.load(std::memory_order_acquire);
+  float* t = d.dft.load(std::memory_order_acquire);
+  if (!s || !t) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    s = d.scratch.load(std::memory_order_acquire);
+    t = d.dft.load(std::memory_order_acquire);
+    if (!s || !t) {
+      void* ps = nullptr;
+      void* pt = nullptr;
+      TS_CUDA(cudaGetSymbolAddress(&ps, g_noalloc_scratch));
+      TS_CUDA(cudaGetSymbolAddress(&pt, g_noalloc_dft));
+      std::vector<float> all(dft_total_floats());
+      const int list[] = {TS_N_LIST};
+      for (int n : list) {
+        std::vector<double> tn;
+        dft_tables(n, tn);
+        std::copy(tn.begin(), tn.end(), all.begin() + dft_constant_offset(n));
+      }
+      TS_CUDA(cudaMemcpy(pt, all.data(), all.size() * sizeof(float), cudaMemcpyHostToDevice));
+      s = static_cast<float*>(ps);
+      t = static_cast<float*>(pt);
+      d.dft.store(t, std::memory_order_release);
+      d.scratch.store(s, std::memory_order_release);
+    }
   }
-  *out = g_noalloc_ptr[dev];
+  *scratch = s;
+  *dft = t;
   return 0;
 }
 
 template <int N>
+int noalloc_preload_kernels() {
+  if (preload_tau<float, N>() || preload_apply_residual<float, N>())
+    return fail(TS_ERR_CUDA, "allocation-free residual: kernel preload failed");
+  return 0;
+}
+
+// set-up done by ts_problem_create on the problem's device
+int noalloc_setup(int N) {
+  float *s = nullptr, *t = nullptr;
+  TS_TRY(noalloc_arrays(&s, &t));
+  TS_DISPATCH(N, (noalloc_preload_kernels<NN>()));
+}
+
+template <int N>
 int residual_noalloc_impl(ts_problem* pr, const float* y, float* r, cudaStream_t st) {
-  constexpr int C = 2 * N, K = 3 * N - 2;
+  constexpr int C = 2 * N;
   const ts_mesh* m = pr->mesh;
-  const size_t dft_n = (size_t)2 * K * C, dft_pad = (dft_n + 63) & ~(size_t)63;
   const size_t tau_n = (size_t)m->E * 4 * pr->NTP, tau_pad = (tau_n + 63) & ~(size_t)63;
   const size_t t0_n = (size_t)m->E * 12 * C;
-  const size_t need = dft_pad + tau_pad + t0_n;
+  const size_t need = tau_pad + t0_n;
   if (need > kNoAllocFloats)
     return fail(TS_ERR_ARG, "ts_residual_noalloc: mesh needs " + std::to_string(need * 4) +
                                 " bytes of scratch, the fixed array holds " +
                                 std::to_string(kNoAllocFloats * 4));
-  float* base = nullptr;
-  TS_TRY(noalloc_scratch(&base));
+  float *base = nullptr, *tables = nullptr;
+  TS_TRY(noalloc_arrays(&base, &tables));
   LinState<float> l;
-  l.dft = base;
-  l.tau = base + dft_pad;
+  l.dft = tables + dft_constant_offset(N);
+  l.tau = base;
   l.t0 = l.tau + tau_pad;
-  // DFT tables, same values as the allocating path (double, rounded to float)
-  thread_local float tab[2 * (3 * 15 - 2) * (2 * 15)];
-  const double pi = 3.14159265358979323846;
-  for (size_t t = 0; t < dft_n; ++t) tab[t] = 0.f;
-  for (int k = 0; k < K; ++k) {
-    tab[k * C + 0] = 1.f;
-    for (int n = 1; n < N; ++n) {
-      const double th = 2.0 * pi * n * k / K;
-      tab[k * C + 2 * n] = (float)(2.0 * std::cos(th));
-      tab[k * C + 2 * n + 1] = (float)(-2.0 * std::sin(th));
-    }
-  }
-  float* inv = tab + K * C;
-  for (int k = 0; k < K; ++k) {
-    inv[0 * K + k] = (float)(1.0 / K);
-    for (int n = 1; n < N; ++n) {
-      const double th = 2.0 * pi * n * k / K;
-      inv[(2 * n) * K + k] = (float)(std::cos(th) / K);
-      inv[(2 * n + 1) * K + k] = (float)(-std::sin(th) / K);
-    }
-  }
-  TS_CUDA(cudaMemcpyAsync(l.dft, tab, dft_n * sizeof(float), cudaMemcpyHostToDevice, st));
   if (launch_tau<float, N>(m->d_tets, m->d_geo32, y, m->E, l.tau, (float)(pr->p.mu / pr->p.rho),
                            (float)pr->p.C_I, pr->d_counter, st))
     return fail(TS_ERR_CUDA, "tau kernel launch failed");
@@ -1011,6 +1526,7 @@ int ts_solve(ts_problem* pr, void* y_inout, const ts_solve_opts* opts, ts_solve_
   if (o.eps_ls <= 0) o.eps_ls = 0.05;
   if (o.max_matvec <= 0) o.max_matvec = 10000;
   if (o.precision != 32 && o.precision != 64) return fail(TS_ERR_ARG, "precision must be 32 or 64");
+  if (o.precond < 0 || o.precond > 3) return fail(TS_ERR_ARG, "ts_solve: precond must be 0, 1, 2 or 3");
   std::memset(rep, 0, sizeof(*rep));
   TS_TRY(sync_dmask(pr));
   const int64_t n = field_len(pr);
@@ -1095,8 +1611,16 @@ int ts_solve(ts_problem* pr, void* y_inout, const ts_solve_opts* opts, ts_solve_
     } else if (rejecting) {
       pr->p.dt_pseudo = dt0 * backoff;
     }
-    // right preconditioner: approximate inverse diagonal of the tangent
-    if (o.precond) TS_TRY(precond_diag(pr, y, pr->d_D, st));
+    // right preconditioner: approximate inverse diagonal of the tangent, or the
+    // inverted nodal diagonal blocks of the tangent at this state
+    if (o.precond) {
+      const double tp = now_s();
+      if (o.precond == 1) TS_TRY(precond_diag(pr, y, pr->d_D, st));
+      else if (o.precond == 2) TS_TRY(block_precond_setup(pr, st));
+      else TS_TRY(sgs_setup(pr, st));
+      TS_CUDA(cudaStreamSynchronize(st));
+      rep->t_precond += now_s() - tp;
+    }
     // GMRES(m) on (H + c1 rho/dt M) D d' = -r, d = D d', from d = 0
     TS_CUDA(cudaMemsetAsync(pr->d_dy, 0, n * sizeof(double), st));
     double bnorm = rn;
@@ -1115,8 +1639,14 @@ int ts_solve(ts_problem* pr, void* y_inout, const ts_solve_opts* opts, ts_solve_
         const double tj = now_s();
         TS_CUDA(cudaEventRecord(pr->ev_a, st));
         double* vk = V + (int64_t)k * n;
-        if (o.precond) {
+        if (o.precond == 1) {
           if (vec_mul(pr->d_t, pr->d_D, vk, n, st)) return fail(TS_ERR_CUDA, "mul");
+          vk = pr->d_t;
+        } else if (o.precond == 2) {
+          TS_TRY(block_apply_any(pr, vk, pr->d_t, st));
+          vk = pr->d_t;
+        } else if (o.precond == 3) {
+          TS_TRY(sgs_apply_any(pr, vk, pr->d_t, st));
           vk = pr->d_t;
         }
         if (o.precision == 32) {
@@ -1181,8 +1711,16 @@ int ts_solve(ts_problem* pr, void* y_inout, const ts_solve_opts* opts, ts_solve_
       double tk = now_s();
       TS_CUDA(cudaMemcpyAsync(pr->d_h, yk.data(), k_used * sizeof(double), cudaMemcpyHostToDevice, st));
       if (krylov_combine(pr->d_w, V, n, k_used, pr->d_h, n, st)) return fail(TS_ERR_CUDA, "combine");
-      if (o.precond && vec_mul(pr->d_w, pr->d_D, pr->d_w, n, st)) return fail(TS_ERR_CUDA, "mul");
-      if (vec_axpy(pr->d_dy, pr->d_w, 1.0, n, st)) return fail(TS_ERR_CUDA, "axpy");
+      const double* upd = pr->d_w;
+      if (o.precond == 1 && vec_mul(pr->d_w, pr->d_D, pr->d_w, n, st)) return fail(TS_ERR_CUDA, "mul");
+      if (o.precond == 2) {
+        TS_TRY(block_apply_any(pr, pr->d_w, pr->d_t, st));
+        upd = pr->d_t;
+      } else if (o.precond == 3) {
+        TS_TRY(sgs_apply_any(pr, pr->d_w, pr->d_t, st));
+        upd = pr->d_t;
+      }
+      if (vec_axpy(pr->d_dy, upd, 1.0, n, st)) return fail(TS_ERR_CUDA, "axpy");
       rep->t_krylov += now_s() - tk;
       double est = std::fabs(g[k_used]);
       lin_res = est;

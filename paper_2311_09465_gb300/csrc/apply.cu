@@ -373,6 +373,22 @@ static int launch_mode(const int4* tets, const T* geo, const T* v, const T* u0, 
   return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
+// Loads the residual's element kernel into the current device's context
+// without launching it (lazy module loading would load it at its first launch).
+template <typename T, int N>
+int preload_apply_residual() {
+  using L = ApplyLayout<N, MODE_RESIDUAL>;
+  int warps = 4;
+  while (warps > 1 && (size_t)(L::TABLES + warps * L::WARP) * sizeof(T) > 200 * 1024) --warps;
+  const size_t smem = (size_t)(L::TABLES + warps * L::WARP) * sizeof(T);
+  if (smem > 227 * 1024) return -6;
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, apply_kernel<T, N, MODE_RESIDUAL>) != cudaSuccess) return -2;
+  return cudaFuncSetAttribute(apply_kernel<T, N, MODE_RESIDUAL>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess
+             ? 0 : -2;
+}
+
 template <typename T, int N>
 int launch_apply(int mode, const int4* tets, const T* geo, const T* v, const T* u0,
                  const T* tau, T* t0cache, const uint8_t* dmask, T* out, const T* dft,
@@ -438,6 +454,29 @@ int launch_outlet(const int32_t* nodes, const T* w, int n_nodes, T R, const T* v
   return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
+template <typename T>
+__global__ void inlet_fill_kernel(const int32_t* __restrict__ nodes, const double* __restrict__ vals,
+                                  int64_t n, int C, T* __restrict__ y) {
+  const int64_t total = n * 3 * C;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = t / (3 * C), r = t - k * 3 * C;
+    y[(int64_t)nodes[k] * 4 * C + r] = (T)vals[t];
+  }
+}
+
+template <typename T>
+int launch_inlet_fill(const int32_t* nodes, const double* vals, int64_t n, int C, T* y, cudaStream_t st) {
+  if (n <= 0) return 0;
+  int64_t blocks = (n * 3 * C + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  count_launches(1);
+  inlet_fill_kernel<T><<<(int)blocks, 256, 0, st>>>(nodes, vals, n, C, y);
+  return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+template int launch_inlet_fill<float>(const int32_t*, const double*, int64_t, int, float*, cudaStream_t);
+template int launch_inlet_fill<double>(const int32_t*, const double*, int64_t, int, double*, cudaStream_t);
+
 template int launch_outlet<float>(const int32_t*, const float*, int, float, const float*,
                                   const uint8_t*, int, float*, int, cudaStream_t);
 template int launch_outlet<double>(const int32_t*, const double*, int, double, const double*,
@@ -448,6 +487,8 @@ template int launch_outlet<double>(const int32_t*, const double*, int, double, c
                                   T*, const uint8_t*, T*, const T*, Phys<T>, int64_t,        \
                                   int64_t, cudaStream_t);
 TS_FOR_EACH_N(TS_INST_APPLY, float)
+#define TS_INST_PRELOAD_APPLY(T, N) template int preload_apply_residual<T, N>();
+TS_FOR_EACH_N(TS_INST_PRELOAD_APPLY, float)
 TS_FOR_EACH_N(TS_INST_APPLY, double)
 
 }  // namespace ts

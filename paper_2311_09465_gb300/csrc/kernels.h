@@ -21,6 +21,13 @@ template <typename T, int N>
 int launch_tau(const int4* tets, const T* geo, const T* y, int64_t n_elem, T* tau_out, T nu,
                T C_I, unsigned* n_unconverged, cudaStream_t st);
 
+// load a kernel into the current device's context without launching it
+// (instantiated for T = float only)
+template <typename T, int N>
+int preload_tau();
+template <typename T, int N>
+int preload_apply_residual();
+
 // FP64 tau from FP32 Jacobi eigenvectors plus an FP64 polish (tau.cu)
 template <int N>
 int launch_tau_polish(const int4* tets, const double* geo, const double* y, int64_t n_elem,
@@ -46,6 +53,11 @@ template <typename T, int N>
 int launch_apply(int mode, const int4* tets, const T* geo, const T* v, const T* u0,
                  const T* tau, T* t0cache, const uint8_t* dmask, T* out, const T* dft,
                  Phys<T> ph, int64_t e0, int64_t e1, cudaStream_t st);
+
+// y[node][i][c] = vals[k][i][c] for the k-th listed node, velocity fields i < 3
+// (the inlet Dirichlet data of the initial guess)
+template <typename T>
+int launch_inlet_fill(const int32_t* nodes, const double* vals, int64_t n, int C, T* y, cudaStream_t st);
 
 // Resistance outlets: out[A][i][c] += R w_Ai Q_c with Q_c = sum_B w_Bi v[B][i][c]
 template <typename T>
@@ -98,6 +110,36 @@ int j32_upload_n123(const float* host_all);
 int j32_upload_n45(const float* host_all);
 int j32_upload_n7(const float* host_all);
 constexpr int J32_MAX_N = 7;   // largest N with the single-launch FP32 kernel
+
+// Nodal diagonal blocks H_AA of the tangent (precond.cu): one 8N x 8N block per
+// node from the node-to-element list (packed element * 4 + local node); with
+// invert the inverse, column-major, else H_AA row-major.  Fixed unknowns
+// (Im(mode 0), Dirichlet velocity) have zero rows and columns (identity when
+// inverted); n_singular counts blocks that could not be inverted (stored as I).
+template <typename T, int N>
+int launch_block_diag(int variant_paper, int invert, const int32_t* node_off, const int32_t* node_elem,
+                      const int4* tets, const T* geo, const T* u0, const T* tau, const uint8_t* dmask,
+                      const float* outdiag, Phys<float> ph, float* out, int64_t n_nodes,
+                      unsigned* n_singular, cudaStream_t st);
+// z[A] = Binv[A] x[A] for every node (FP32 blocks, FP64 vectors)
+template <int N>
+int launch_block_apply(const float* binv, const double* x, double* z, int64_t n_nodes, cudaStream_t st);
+
+// Assembled tangent of the paper's variant (assembled.cu): per node-graph
+// connection a record of assembled_record_floats(N) floats (K, L, G_1..3, D_1..3)
+template <typename T, int N>
+int launch_assemble_paper(const int32_t* node_off, const int32_t* node_elem, const int32_t* row_off,
+                          const int32_t* cols, const int4* tets, const T* geo, const T* u0, const T* tau,
+                          Phys<float> ph, float* H, int64_t n_nodes, cudaStream_t st);
+template <int N>
+int launch_spmv_paper(const int32_t* row_off, const int32_t* cols, const float* H, const uint8_t* dmask,
+                      const float* x, float* y, int64_t n_nodes, cudaStream_t st);
+int assembled_record_floats(int N);
+// one colour of a block Gauss-Seidel sweep: z_A = Binv_A (r_A - sum_{B != A} H_AB z_B)
+template <int N>
+int launch_sgs_colour(const int32_t* rows, int64_t n_rows, const int32_t* row_off, const int32_t* cols,
+                      const float* H, const float* binv, const uint8_t* dmask, const float* r, float* z,
+                      cudaStream_t st);
 
 // FP64 Krylov helpers (krylov.cu)
 // h_out[j] = basis_j . w (j < nvec), with self also h_out[nvec] = w . w;

@@ -167,6 +167,17 @@ int launch_tau(const int4* tets, const T* geo, const T* y, int64_t n_elem, T* ta
   return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
+// Loads tau_kernel<T, N> into the current device's context without launching
+// it (with lazy module loading a kernel is otherwise loaded at its first launch).
+template <typename T, int N>
+int preload_tau() {
+  using L = TauLayout<N>;
+  cudaFuncAttributes a;
+  if (cudaFuncGetAttributes(&a, tau_kernel<T, N>) != cudaSuccess) return -2;
+  const size_t smem = (size_t)4 * L::WARP * sizeof(T);
+  return cudaFuncSetAttribute(tau_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+                 cudaSuccess ? 0 : -2;
+}
 
 // ---------------------------------------------------------------------------
 // FP64 tau from FP32 eigenvectors.  The FP32 Jacobi gives V32 with
@@ -581,6 +592,8 @@ TS_FOR_EACH_N(TS_INST_BACKFLOW, double)
 #define TS_INST_TAU(T, N)                                                                 \
   template int launch_tau<T, N>(const int4*, const T*, const T*, int64_t, T*, T, T,       \
                                 unsigned*, cudaStream_t);
+#define TS_INST_PRELOAD_TAU(T, N) template int preload_tau<T, N>();
+TS_FOR_EACH_N(TS_INST_PRELOAD_TAU, float)
 TS_FOR_EACH_N(TS_INST_TAU, float)
 TS_FOR_EACH_N(TS_INST_TAU, double)
 

@@ -28,6 +28,23 @@ def test_tangent_bytes_at_the_junction():
     assert bench._jvp_bytes(c) == expect == 429_211_416
 
 
+def test_tangent_roofline_bytes_model_at_the_junction():
+    import bench
+    # v, Hv (8N per node), u0 velocity (6N per node), connectivity, coordinates,
+    # packed tau (4 points x 91 entries): 300.7 MB at the 188k-tet junction
+    V, E = 38_250, 187_989
+    expect = V * 56 * 4 + V * 42 * 4 + V * 56 * 4 + 16 * E + 12 * V + E * 4 * 91 * 4
+    assert bench._jvp_bytes_model(_Case(7, E, V)) == expect == 300_740_808
+
+
+def test_tau_flop_model():
+    import bench
+    # 45 n_m^3 flops per quadrature point, n_m = 2N - 1, 4 points per element
+    assert bench._tau_flops(_Case(7, 187_989, 38_250)) == 4 * 187_989 * 45 * 13 ** 3
+    assert abs(bench._tau_flops(_Case(7, 187_989, 38_250)) - 7.44e10) < 0.01e10
+    assert bench._tau_flops(_Case(1, 3, 4)) == 4 * 3 * 45
+
+
 def test_tau_dd_instruction_model():
     import bench
     # per point at N = 7 (n = 13, t = 91): 15 instructions per double-float

@@ -103,8 +103,12 @@ def test_pod_basis_and_coefficients_match_oracle(torch):
         k = np.argmax(np.abs(A_ref[:, j]))
         if np.sign(A[k, j]) != np.sign(A_ref[k, j]):
             A[:, j] *= -1
+    # the basis is stored in FP32: a coefficient along direction j picks up the
+    # FP32 rounding of phi_j along the stronger directions, a relative error of
+    # about u32 (sigma_1 / sigma_j); the bar scales with that ratio
     for j in range(8):
-        assert rel_l2(A[:, j], A_ref[:, j]) <= 1e-4, (j, rel_l2(A[:, j], A_ref[:, j]))
+        tol = 1e-5 * sig_ref[0] / sig_ref[j]
+        assert rel_l2(A[:, j], A_ref[:, j]) <= tol, (j, rel_l2(A[:, j], A_ref[:, j]), tol)
 
 
 def _pipe_sample(rng, mesh):
