@@ -74,10 +74,16 @@ def _library_inflow(g, case):
     inflow waveform's flow-rate coefficients) and the paper's initial guess
     (ts_initial_guess): a new FP64 CUDA field."""
     from workloads import meshgen as mg
-    radius = {tag: R for _, _, R, tag in mg.JUNCTION_ARMS}
-    for tag in (mg.TAG_INLET1, mg.TAG_INLET2):
-        Q = np.asarray(case.info["waves"][tag]) * np.pi * radius[tag] ** 2
-        g.set_inlet(tag, Q, "parabolic")
+    for ax, sg, R, tag in mg.JUNCTION_ARMS:
+        if tag not in (mg.TAG_INLET1, mg.TAG_INLET2):
+            continue
+        # the arm's axis passes through the origin; inflow points along -sg * axis
+        direction = np.zeros(3)
+        direction[mg._AX[ax]] = -sg
+        centre = np.zeros(3)
+        centre[mg._AX[ax]] = sg * case.mesh.info.get("arm_len", 6.0)
+        Q = np.asarray(case.info["waves"][tag]) * np.pi * R ** 2
+        g.set_inlet(tag, Q, "parabolic", centre=centre, direction=direction, radius=R)
     return g.initial_guess()
 
 
@@ -704,6 +710,70 @@ def run_sweep(args):
                       "rows": out}), flush=True)
 
 
+def _spectral_l2(y, n_modes=None):
+    """Space-time L2 norm of a modal field [V, 4, N, 2] over the period (Parseval:
+    |f|^2 = |f_0|^2 + 2 sum_{n>=1} |f_n|^2), velocity fields only."""
+    u = y[:, 0:3]
+    w = np.full(u.shape[2], 2.0)
+    w[0] = 1.0
+    return float(np.sqrt(np.sum(w[None, None, :, None] * u ** 2)))
+
+
+def mode_error(y_N, y_ref):
+    """Relative space-time L2 error of an N-mode field against a reference with
+    more modes (the missing modes count as error)."""
+    N = y_N.shape[2]
+    d = y_ref.copy()
+    d[:, :, :N] -= y_N
+    return _spectral_l2(d) / _spectral_l2(y_ref)
+
+
+def run_mode_study(args, Ns=(2, 3, 5, 7, 10), N_ref=15, h=0.3, Re=100.0, Wo=10.0, amp=0.4):
+    """Solution error against the number of modes, on the junction with a
+    waveform rich in harmonics: every solve iterates to 1e-10 r_ref (mixed
+    precision, block Gauss-Seidel preconditioner); the N-mode fields are
+    compared with the N_ref-mode field (space-time L2 of the velocity, the
+    missing modes counted as error), beside the truncation error of the inflow
+    waveform itself (one JSON line)."""
+    import torch
+
+    import paper_2311_09465_gb300 as ts
+    from workloads import cases, meshgen as mg
+
+    mesh = mg.junction(h=h, seed=1)
+    waves = {tag: cases.waveform_random(N_ref, 300 + k, amp=amp) for k, tag in enumerate((mg.TAG_INLET1,
+                                                                                         mg.TAG_INLET2))}
+    fields, rows = {}, []
+    for N in tuple(Ns) + (N_ref,):
+        case = cases.junction_case(N=N, Re=Re, Wo=Wo, wave_seed=300, resistance=1.0, mesh=mesh, amp=amp)
+        case.info["waves"] = {tag: w[:N] for tag, w in waves.items()}
+        g = ts.GLSProblem(case, variant="lin_a", dt_pseudo=0.2)
+        y = _library_inflow(g, case)
+        r_ref = float(g.residual(y).norm())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rep = g.solve(y, precision=32, tol=1e-10, r_ref=r_ref, max_steps=150, krylov=100, eps_ls=0.05,
+                      max_matvec=2000, precond=3, ser=1.0, dt_max=8.0, raise_on_noconv=False)
+        torch.cuda.synchronize()
+        fields[N] = y.cpu().numpy()
+        rows.append({"N": N, "seconds": time.perf_counter() - t0, "steps": rep["steps"],
+                     "matvecs": rep["matvecs"], "r_final": rep["r_final"], "converged": rep["status"] == 0})
+        g.close()
+    ref = fields[N_ref]
+    wref = np.concatenate([w for w in waves.values()])
+    wnorm = np.sqrt(sum(abs(w[0]) ** 2 + 2 * np.sum(np.abs(w[1:]) ** 2) for w in waves.values()))
+    for row in rows:
+        N = row["N"]
+        row["field_rel_l2_vs_ref"] = mode_error(fields[N], ref) if N != N_ref else 0.0
+        row["inflow_truncation_rel_l2"] = float(np.sqrt(sum(2 * np.sum(np.abs(w[N:]) ** 2)
+                                                            for w in waves.values())) / wnorm)
+    out = {"study": "mode count", "workload": f"junction {mesh.n_tets} tets, Re {Re}, Wo {Wo}, "
+           f"inflow 1/n^2 x {amp} to harmonic {N_ref - 1}", "reference_N": N_ref, "rows": rows}
+    if args is not None:
+        print(json.dumps(out), flush=True)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -717,10 +787,14 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=400)
     ap.add_argument("--ref-sample", type=int, default=200)
+    ap.add_argument("--mode-study", action="store_true",
+                    help="solution error vs number of modes against a 15-mode reference (its own JSON line)")
     ap.add_argument("--sweep", action="store_true",
                     help="mode sweep N = 3, 7, 15 on the junction (its own JSON line) instead of the bench")
     args = ap.parse_args()
-    if args.sweep:
+    if args.mode_study:
+        run_mode_study(args)
+    elif args.sweep:
         run_sweep(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -59,6 +59,9 @@ extern "C" {
 #define TS_JVP_PAPER   0   /* A, tau frozen; LS parts of G_i, D_j dropped (section 2.5.2) */
 #define TS_JVP_FROZEN  1   /* A, tau frozen; all blocks of eq. (K_mat)                    */
 #define TS_JVP_LIN_A   2   /* FROZEN + derivative of A_j (tau frozen): exact up to d tau   */
+#define TS_JVP_EXACT   3   /* LIN_A + the derivative of tau (Daleckii-Krein, from the      */
+                           /* eigenpairs of M): the exact Jacobian of eq. (Rmc); FP32     */
+                           /* tangent products with N <= 7 only (TS_ERR_UNSUPPORTED else) */
 
 /* ts_problem_option keys and values (implementation choices, not physics) */
 #define TS_OPT_TAU64        1  /* how the FP64 residual computes tau (eq. 3D-tau):          */
@@ -69,6 +72,10 @@ extern "C" {
 #define TS_TAU64_JACOBI     2  /*   FP64 Jacobi eigenpairs                                 */
 #define TS_OPT_FP32_TANGENT 2  /* FP32 tangent products: 0 single launch with vector       */
                                /* atomics (default), 1 colour-ordered launches            */
+#define TS_OPT_ELEMENT64    3  /* arithmetic of the FP64 element operator (the FP64         */
+                               /* residual's element pass and FP64 tangent products):     */
+#define TS_ELEMENT64_NATIVE 0  /*   FP64 instructions                                     */
+#define TS_ELEMENT64_DOUBLEFLOAT 1 /* double-float pairs on the FP32 pipe (FP64 storage)  */
 
 typedef struct ts_mesh ts_mesh;
 typedef struct ts_problem ts_problem;
@@ -182,12 +189,15 @@ int  ts_set_bc(ts_problem* prob, int tag, int kind, double value);
 /* Inflow boundary data (section 2.4: the Dirichlet data g are expanded in the
  * same Fourier modes as the unknowns, eq. upgh_def, g_n = (1/T) int g e^{-i n w t};
  * section 3.1 prescribes a parabolic inlet profile scaled by the flow waveform).
- * The boundary triangles with this tag form a circular inlet; the library
- * takes its inflow direction from their area-weighted normal (pointing into
- * the domain), and its centre and radius R from a least-squares circle
- * (Kasa's algebraic fit) through the rim: the tag's nodes that also lie on
- * triangles of other tags.  For each mode n = 0..N-1 the velocity at an
- * inlet node at distance r from the axis is w_n(r) times the inflow
+ * The boundary triangles with this tag form a circular inlet.  Its geometry
+ * is the caller's (geometry_host: centre xyz, inflow direction xyz pointing
+ * into the domain, radius R; copied) or, with geometry_host NULL, derived
+ * from the triangles: the inflow direction from their area-weighted normal,
+ * the centre from their area-weighted centroid, and R as the largest
+ * distance from the axis of a rim node (a node of the tag that also lies on
+ * triangles of other tags; right when the rim lies on the circle, as on a
+ * pipe meshed to its wall).  For each mode n = 0..N-1 the velocity at an
+ * inlet node at distance r from the axis is w_n(min(r, R)) times the inflow
  * direction, with w_n the profile of mean velocity U_n = Q_n / (pi R^2):
  *   TS_PROFILE_PARABOLIC  w_n = 2 U_n (1 - r^2/R^2)
  *   TS_PROFILE_WOMERSLEY  w_0 parabolic; w_n = U_n [1 - J0(L r/R)/J0(L)] /
@@ -199,8 +209,10 @@ int  ts_set_bc(ts_problem* prob, int tag, int kind, double value);
  *   Qn_host  [N][2] flow-rate coefficients (re, im) of modes 0..N-1, copied;
  *            Im(Q_0) is ignored (the mean flow is real, section 3.3)
  * A second call for the same tag replaces the first.  TS_ERR_ARG for an
- * unknown profile, a tag without triangles, or a rim of fewer than 3 nodes. */
-int  ts_set_inlet(ts_problem* prob, int tag, const double* Qn_host, int profile);
+ * unknown profile, a tag without triangles, a rim of fewer than 3 nodes, or
+ * a zero direction or radius. */
+int  ts_set_inlet(ts_problem* prob, int tag, const double* Qn_host, int profile,
+                  const double* geometry_host);
 /* Geometry ts_set_inlet derived for a tag: out_host[0..2] centre, [3..5] unit
  * inflow direction, [6] radius.  TS_ERR_ARG if the tag has no inlet data. */
 int  ts_inlet_info(const ts_problem* prob, int tag, double* out_host);
@@ -379,6 +391,31 @@ int  ts_surrogate_train(ts_surrogate* sur, const float* X_host, const double* Y,
 /* y_inout (FP64 field of prob) <- ybar + Phi diag(sigma) f(x) on the free
  * entries; Dirichlet velocity values and Im(mode 0) keep their input */
 int  ts_surrogate_guess(ts_surrogate* sur, ts_problem* prob, const float* x_host, double* y_inout,
+                        void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Time-spectral GLS convection-diffusion of a scalar (a passive tracer),
+ * eq. (3D-weak) with eq. (3D-weak-def), section 2.2: for a given advecting
+ * velocity a (modes at the nodes) and diffusivity kappa the residual
+ *   r_A = int N_A (Omega phi + A_i dphi/dx_i) + kappa dN_A/dx_i dphi/dx_i
+ *       + int (-Omega N_A + A_i dN_A/dx_i) tau (Omega phi + A_i dphi/dx_i)
+ * with A_i = A(a_i) (eq. phi-def) and tau of eq. (3D-tau) with kappa, at every
+ * quadrature point.  It is linear in phi (its own tangent).  Rows of
+ * Dirichlet nodes and Im(mode 0) are zero; zero Neumann data elsewhere.
+ * ------------------------------------------------------------------------- */
+typedef struct ts_tracer ts_tracer;
+/* TS_ERR_UNSUPPORTED if no kernel is compiled for N.  The mesh must outlive it. */
+int  ts_tracer_create(const ts_mesh* mesh, int N, double kappa, double omega, double C_I,
+                      ts_tracer** out);
+void ts_tracer_free(ts_tracer* tracer);
+/* nodes of the boundary triangles with this tag carry Dirichlet data (no equation) */
+int  ts_tracer_set_dirichlet(ts_tracer* tracer, int tag);
+/* r(phi) for the advecting velocity a: caller-owned device arrays of the
+ * given precision, a [V][3][N][2] (the velocity part of a modal field), phi and
+ * r [V][N][2] (one field of the modal layout).  Computes tau at every point
+ * (FP64: the double-float refinement; FP32: FP32 Jacobi) into library-owned
+ * buffers allocated at the first call.  r may not alias a or phi. */
+int  ts_tracer_residual(ts_tracer* tracer, const void* a, const void* phi, void* r, int precision,
                         void* stream);
 
 /* Thread-local message describing the last error. */

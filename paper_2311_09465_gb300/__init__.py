@@ -23,9 +23,10 @@ TS_OK, TS_ERR_ARG, TS_ERR_CUDA, TS_ERR_OOM, TS_ERR_NOCONV, TS_ERR_NAN, TS_ERR_UN
 TS_BC_DIRICHLET, TS_BC_TRACTION, TS_BC_RESISTANCE, TS_BC_BACKFLOW = 1, 2, 3, 4
 TS_PROFILE_PARABOLIC, TS_PROFILE_WOMERSLEY = 1, 2
 PROFILES = {"parabolic": TS_PROFILE_PARABOLIC, "womersley": TS_PROFILE_WOMERSLEY}
-TS_JVP_PAPER, TS_JVP_FROZEN, TS_JVP_LIN_A = 0, 1, 2
-VARIANTS = {"paper": TS_JVP_PAPER, "frozen": TS_JVP_FROZEN, "lin_a": TS_JVP_LIN_A}
-TS_OPT_TAU64, TS_OPT_FP32_TANGENT = 1, 2
+TS_JVP_PAPER, TS_JVP_FROZEN, TS_JVP_LIN_A, TS_JVP_EXACT = 0, 1, 2, 3
+VARIANTS = {"paper": TS_JVP_PAPER, "frozen": TS_JVP_FROZEN, "lin_a": TS_JVP_LIN_A, "exact": TS_JVP_EXACT}
+TS_OPT_TAU64, TS_OPT_FP32_TANGENT, TS_OPT_ELEMENT64 = 1, 2, 3
+ELEMENT64 = {"native": 0, "doublefloat": 1}
 TS_TAU64_REFINE, TS_TAU64_DOUBLEFLOAT, TS_TAU64_JACOBI = 0, 1, 2
 TAU64 = {"refine": TS_TAU64_REFINE, "doublefloat": TS_TAU64_DOUBLEFLOAT, "jacobi": TS_TAU64_JACOBI}
 SUPPORTED_N = (1, 2, 3, 4, 5, 7, 10, 15)
@@ -86,7 +87,7 @@ def lib() -> ctypes.CDLL:
     L.ts_problem_set.argtypes = [vp, ctypes.c_double, ctypes.c_int]
     L.ts_set_bc.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double]
     L.ts_problem_option.argtypes = [vp, ctypes.c_int, ctypes.c_int]
-    L.ts_set_inlet.argtypes = [vp, ctypes.c_int, dp, ctypes.c_int]
+    L.ts_set_inlet.argtypes = [vp, ctypes.c_int, dp, ctypes.c_int, dp]
     L.ts_inlet_info.argtypes = [vp, ctypes.c_int, dp]
     L.ts_initial_guess.argtypes = [vp, vp, ctypes.c_int, vp]
     L.ts_residual.argtypes = [vp, vp, vp, ctypes.c_int, vp]
@@ -125,6 +126,12 @@ def lib() -> ctypes.CDLL:
     L.ts_batch_solve.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(ts_solve_opts),
                                  ctypes.POINTER(ts_solve_report), vp]
     L.ts_batch_launch_shape.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    L.ts_tracer_create.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                   ctypes.POINTER(vp)]
+    L.ts_tracer_free.argtypes = [vp]
+    L.ts_tracer_free.restype = None
+    L.ts_tracer_set_dirichlet.argtypes = [vp, ctypes.c_int]
+    L.ts_tracer_residual.argtypes = [vp, vp, vp, vp, ctypes.c_int, vp]
     L.ts_last_error.restype = ctypes.c_char_p
     L.ts_version.restype = ctypes.c_char_p
     L.ts_launch_count.restype = ctypes.c_int64
@@ -226,12 +233,19 @@ def ts_set_bc(prob, tag: int, kind: int, value: float = 0.0):
     _check(lib().ts_set_bc(prob, tag, kind, value))
 
 
-def ts_set_inlet(prob, tag: int, Qn, profile="parabolic"):
-    """Inlet Dirichlet data from complex flow-rate coefficients Qn (modes 0..N-1)."""
+def ts_set_inlet(prob, tag: int, Qn, profile="parabolic", centre=None, direction=None, radius=None):
+    """Inlet Dirichlet data from complex flow-rate coefficients Qn (modes 0..N-1);
+    the inlet geometry is derived from the mesh unless centre, direction (into the
+    domain) and radius are all given."""
     q = np.asarray(Qn, dtype=np.complex128)
     buf = np.ascontiguousarray(np.stack([q.real, q.imag], axis=1), dtype=np.float64)
+    geo = None
+    if centre is not None:
+        gbuf = np.ascontiguousarray(np.concatenate([np.asarray(centre, np.float64),
+                                                    np.asarray(direction, np.float64), [float(radius)]]))
+        geo = gbuf.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     _check(lib().ts_set_inlet(prob, tag, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                              PROFILES[profile] if isinstance(profile, str) else int(profile)))
+                              PROFILES[profile] if isinstance(profile, str) else int(profile), geo))
 
 
 def ts_inlet_info(prob, tag: int) -> dict:
@@ -321,7 +335,7 @@ class GLSProblem:
     """Mesh + problem handles for a seeded case (``workloads.cases.Case``)."""
 
     def __init__(self, case, variant="lin_a", dt_pseudo=math.inf, tau64="doublefloat",
-                 fp32_tangent="single"):
+                 fp32_tangent="single", element64=None):
         m = case.mesh
         self.case = case
         self.N = case.N
@@ -336,18 +350,21 @@ class GLSProblem:
             ts_set_bc(self.prob, tag, TS_BC_RESISTANCE, R)
         for tag, beta in getattr(case, "backflow", {}).items():
             ts_set_bc(self.prob, tag, TS_BC_BACKFLOW, beta)
-        self.option(tau64=tau64, fp32_tangent=fp32_tangent)
+        self.option(tau64=tau64, fp32_tangent=fp32_tangent, element64=element64)
 
-    def option(self, tau64=None, fp32_tangent=None):
-        """tau64: "refine" | "doublefloat" | "jacobi"; fp32_tangent: "single" | "coloured"."""
+    def option(self, tau64=None, fp32_tangent=None, element64=None):
+        """tau64: "refine" | "doublefloat" | "jacobi"; fp32_tangent: "single" | "coloured";
+        element64: "native" | "doublefloat"."""
+        if element64 is not None:
+            ts_problem_option(self.prob, TS_OPT_ELEMENT64, ELEMENT64[element64])
         if tau64 is not None:
             ts_problem_option(self.prob, TS_OPT_TAU64, TAU64[tau64])
         if fp32_tangent is not None:
             ts_problem_option(self.prob, TS_OPT_FP32_TANGENT,
                               {"single": 0, "coloured": 1}[fp32_tangent])
 
-    def set_inlet(self, tag, Qn, profile="parabolic"):
-        ts_set_inlet(self.prob, tag, Qn, profile)
+    def set_inlet(self, tag, Qn, profile="parabolic", centre=None, direction=None, radius=None):
+        ts_set_inlet(self.prob, tag, Qn, profile, centre, direction, radius)
 
     def inlet_info(self, tag):
         return ts_inlet_info(self.prob, tag)
@@ -646,6 +663,59 @@ class Surrogate:
     def close(self):
         if getattr(self, "h", None):
             lib().ts_surrogate_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ tracer (eq. 3D-weak)
+
+def ts_tracer_create(mesh, N, kappa, omega, C_I=3.0):
+    h = ctypes.c_void_p()
+    _check(lib().ts_tracer_create(mesh, N, kappa, omega, C_I, ctypes.byref(h)))
+    return h
+
+
+def ts_tracer_free(tracer):
+    lib().ts_tracer_free(tracer)
+
+
+def ts_tracer_set_dirichlet(tracer, tag):
+    _check(lib().ts_tracer_set_dirichlet(tracer, tag))
+
+
+def ts_tracer_residual(tracer, a, phi, r, stream=None):
+    import torch
+    for t in (a, phi, r):
+        if not t.is_cuda or not t.is_contiguous() or t.dtype != phi.dtype:
+            raise ValueError("a, phi, r must be contiguous CUDA tensors of one dtype")
+    p = 64 if phi.dtype == torch.float64 else 32
+    _check(lib().ts_tracer_residual(tracer, ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(phi.data_ptr()),
+                                    ctypes.c_void_p(r.data_ptr()), p, _stream_ptr(stream)))
+    return r
+
+
+class Tracer:
+    """Time-spectral GLS convection-diffusion residual of a scalar on a mesh
+    (ts_tracer_*); phi and r are CUDA tensors [V, N, 2], the velocity a [V, 3, N, 2]."""
+
+    def __init__(self, mesh_handle, n_nodes, N, kappa, omega, C_I=3.0, dirichlet_tags=()):
+        self.h = ts_tracer_create(mesh_handle, N, kappa, omega, C_I)
+        self.N, self.n_nodes = N, n_nodes
+        for tag in dirichlet_tags:
+            ts_tracer_set_dirichlet(self.h, tag)
+
+    def residual(self, a, phi, r=None, stream=None):
+        import torch
+        return ts_tracer_residual(self.h, a, phi, torch.empty_like(phi) if r is None else r, stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            ts_tracer_free(self.h)
             self.h = None
 
     def __del__(self):

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libtsgls.so")
-SOURCES = ["api.cu", "tau.cu", "tau_dd.cu", "surrogate.cu", "batch.cu", "jvp32_batch.cu", "apply.cu", "krylov.cu", "precond.cu", "assembled.cu", "jvp32_n123.cu", "jvp32_n45.cu", "jvp32_n7.cu"]
+SOURCES = ["api.cu", "tau.cu", "tau_dd.cu", "surrogate.cu", "batch.cu", "jvp32_batch.cu", "apply.cu", "krylov.cu", "precond.cu", "assembled.cu", "dtau.cu", "jvp32_n123.cu", "jvp32_n45.cu", "jvp32_n7.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

@@ -72,6 +72,8 @@ struct LinState {
   T* u0t = nullptr;     // [V][K][4] u0 velocity sampled in time (FP32 fast path)
   T* vt = nullptr;      // [V][K][4] scratch of the FP32 fast path: the product's input sampled
   T* bneg = nullptr;    // [backflow points][NT_PAD] |A_n|_- (section 2.6)
+  T* l0 = nullptr;      // [E][4][3][C] strong residual L(u0) (exact tangent)
+  bool exact_valid = false;   // l0 and the eigenpair cache belong to this state
   int64_t bneg_points = 0;
   bool valid = false;
 };
@@ -128,6 +130,8 @@ struct ts_problem {
   float *d_v32 = nullptr, *d_w32 = nullptr;
   double *d_D = nullptr, *d_t = nullptr;      // preconditioner diagonal (inverted), temp
   float* d_binv = nullptr;                    // inverted nodal blocks [V][8N][8N] (block Jacobi)
+  float* d_eig = nullptr;                     // eigenpairs of M per point [E*4][EIG] (exact tangent)
+  float* d_dT = nullptr;                      // d tau[v] L(u0) per point [E][4][3][C] (exact tangent)
   float* d_hasm = nullptr;                    // assembled PAPER tangent records [nnzb][2C^2 + 8]
   float *d_r32 = nullptr, *d_z32 = nullptr;   // block Gauss-Seidel work vectors
   bool hasm_valid = false;
@@ -140,6 +144,7 @@ struct ts_problem {
   bool sev_res = false, sev_jvp = false;
   bool fast32 = true;    // FP32 products with the single-launch kernel (jvp32.cu)
   int tau64 = TS_TAU64_DOUBLEFLOAT;  // how the FP64 residual computes tau
+  int elem64 = TS_ELEMENT64_NATIVE;  // arithmetic of the FP64 element operator
 };
 
 // ------------------------------------------------------------------ helpers
@@ -226,6 +231,7 @@ static void lin_free(LinState<T>& l) {
   dfree(l.u0t);
   dfree(l.vt);
   dfree(l.bneg);
+  dfree(l.l0);
   l.bneg_points = 0;
   l.valid = false;
 }
@@ -274,12 +280,24 @@ static Phys<T> phys_of(const ts_problem* pr, bool with_mass) {
 // dispatch on the compiled mode counts
 template <typename T, int N>
 static int apply_colours(ts_problem* pr, int mode, const T* v, const T* u0, LinState<T>& l,
-                         T* out, bool with_mass, cudaStream_t st) {
+                         T* out, bool with_mass, cudaStream_t st, T* l0 = nullptr) {
   const ts_mesh* m = pr->mesh;
   Phys<T> ph = phys_of<T>(pr, with_mass);
   for (size_t c = 0; c + 1 < m->colour_off.size(); ++c) {
-    int rc = launch_apply<T, N>(mode, m->d_tets, geo_of<T>(m), v, u0, l.tau, l.t0, pr->d_dmask,
-                                out, l.dft, ph, m->colour_off[c], m->colour_off[c + 1], st);
+    int rc;
+    if constexpr (sizeof(T) == 8) {
+      if (pr->elem64 == TS_ELEMENT64_DOUBLEFLOAT)
+        rc = launch_apply_dd<N>(mode, m->d_tets, m->d_geo64, (const double*)v, (const double*)u0,
+                                (const double*)l.tau, (double*)l.t0, pr->d_dmask, (double*)out,
+                                (const double*)l.dft, phys_of<double>(pr, with_mass), m->colour_off[c],
+                                m->colour_off[c + 1], st, (double*)l0);
+      else
+        rc = launch_apply<T, N>(mode, m->d_tets, geo_of<T>(m), v, u0, l.tau, l.t0, pr->d_dmask,
+                                out, l.dft, ph, m->colour_off[c], m->colour_off[c + 1], st, l0);
+    } else {
+      rc = launch_apply<T, N>(mode, m->d_tets, geo_of<T>(m), v, u0, l.tau, l.t0, pr->d_dmask,
+                              out, l.dft, ph, m->colour_off[c], m->colour_off[c + 1], st, l0);
+    }
     if (rc) return fail(rc == -6 ? TS_ERR_UNSUPPORTED : TS_ERR_CUDA, "element kernel launch failed");
   }
   const bool mask_input = mode != MODE_RESIDUAL;
@@ -337,26 +355,34 @@ static int residual_impl(ts_problem* pr, const T* y, T* r, cudaStream_t st) {
   TS_TRY(lin_alloc(pr, l));
   const int64_t n = field_len(pr);
   TS_CUDA(cudaMemcpyAsync(l.u0, y, n * sizeof(T), cudaMemcpyDeviceToDevice, st));
+  // the exact tangent also needs the eigenpairs of M and the strong residual
+  const bool exact = pr->p.jvp_variant == TS_JVP_EXACT;
+  float* eig = nullptr;
+  if (exact) {
+    if (!pr->d_eig) TS_TRY(dalloc(&pr->d_eig, (size_t)m->E * 4 * Dims<N>::EIG));
+    if (!l.l0) TS_TRY(dalloc(&l.l0, (size_t)m->E * 12 * pr->C));
+    eig = pr->d_eig;
+  }
   TS_CUDA(cudaEventRecord(pr->sev[0], st));
   int rc;
   if constexpr (sizeof(T) == 8) {
     if (pr->tau64 == TS_TAU64_JACOBI)
       rc = launch_tau<T, N>(m->d_tets, geo_of<T>(m), y, m->E, l.tau, (T)(pr->p.mu / pr->p.rho),
-                            (T)pr->p.C_I, pr->d_counter, st);
+                            (T)pr->p.C_I, pr->d_counter, st, eig);
     else if (pr->tau64 == TS_TAU64_DOUBLEFLOAT)
       rc = launch_tau_dd<N>(m->d_tets, m->d_geo64, (const double*)y, m->E, (double*)l.tau,
-                            pr->p.mu / pr->p.rho, pr->p.C_I, pr->d_counter, st);
+                            pr->p.mu / pr->p.rho, pr->p.C_I, pr->d_counter, st, eig);
     else
       rc = launch_tau_polish<N>(m->d_tets, m->d_geo64, (const double*)y, m->E, (double*)l.tau,
-                                pr->p.mu / pr->p.rho, pr->p.C_I, pr->d_counter, st);
+                                pr->p.mu / pr->p.rho, pr->p.C_I, pr->d_counter, st, eig);
   } else {
     rc = launch_tau<T, N>(m->d_tets, geo_of<T>(m), y, m->E, l.tau, (T)(pr->p.mu / pr->p.rho),
-                          (T)pr->p.C_I, pr->d_counter, st);
+                          (T)pr->p.C_I, pr->d_counter, st, eig);
   }
   if (rc) return fail(TS_ERR_CUDA, "tau kernel launch failed");
   TS_CUDA(cudaEventRecord(pr->sev[1], st));
   TS_CUDA(cudaMemsetAsync(r, 0, n * sizeof(T), st));
-  TS_TRY(apply_colours<T, N>(pr, MODE_RESIDUAL, y, y, l, r, false, st));
+  TS_TRY(apply_colours<T, N>(pr, MODE_RESIDUAL, y, y, l, r, false, st, exact ? l.l0 : nullptr));
   TS_CUDA(cudaEventRecord(pr->sev[2], st));
   pr->sev_res = true;
   TS_TRY(bneg_alloc(pr, l));
@@ -366,6 +392,7 @@ static int residual_impl(ts_problem* pr, const T* y, T* r, cudaStream_t st) {
       return fail(TS_ERR_CUDA, "node sample kernel failed");
   }
   l.valid = true;
+  l.exact_valid = exact;
   pr->hasm_valid = false;
   // the other precision's state is now stale
   if (sizeof(T) == 4) pr->l64.valid = false; else pr->l32.valid = false;
@@ -378,6 +405,12 @@ static int convert_lin(ts_problem* pr, LinState<D>& dst, LinState<S>& src, cudaS
   const ts_mesh* m = pr->mesh;
   const int64_t n_u = field_len(pr), n_tau = m->E * 4 * pr->NTP, n_t0 = m->E * 12 * pr->C;
   int rc = 0;
+  dst.exact_valid = src.exact_valid && src.l0;
+  if (src.l0) {
+    if (!dst.l0) TS_TRY(dalloc(&dst.l0, (size_t)n_t0));
+    if (sizeof(D) == 4) rc |= vec_cast_d2f((float*)dst.l0, (const double*)src.l0, n_t0, st);
+    else rc |= vec_cast_f2d((double*)dst.l0, (const float*)src.l0, n_t0, st);
+  }
   if (sizeof(D) == 4) {
     rc |= vec_cast_d2f((float*)dst.u0, (const double*)src.u0, n_u, st);
     rc |= vec_cast_d2f((float*)dst.tau, (const double*)src.tau, n_tau, st);
@@ -405,6 +438,7 @@ static int mode_of_variant(int v) {
     case TS_JVP_PAPER: return MODE_JVP_PAPER;
     case TS_JVP_FROZEN: return MODE_JVP_FROZEN;
     case TS_JVP_LIN_A: return MODE_JVP_LIN_A;
+    case TS_JVP_EXACT: return MODE_JVP_EXACT;
   }
   return -1;
 }
@@ -422,12 +456,25 @@ static int jvp_impl(ts_problem* pr, const T* v, T* hv, cudaStream_t st) {
   }
   const int mode = mode_of_variant(pr->p.jvp_variant);
   if (mode < 0) return fail(TS_ERR_ARG, "unknown jvp variant");
+  if (mode == MODE_JVP_EXACT) {
+    if (sizeof(T) != 4 || N > J32_MAX_N || !pr->fast32)
+      return fail(TS_ERR_UNSUPPORTED, "ts_jvp: the exact tangent runs in FP32 with N <= 7 (single launch)");
+    if (!pr->d_eig || !l.l0 || !l.exact_valid)
+      return fail(TS_ERR_ARG, "ts_jvp: the exact tangent needs a residual computed with TS_JVP_EXACT set");
+  }
   if constexpr (sizeof(T) == 4 && N <= J32_MAX_N) if (pr->fast32) {
     // the node pre-pass of the product clears hv
     const ts_mesh* m = pr->mesh;
-    const J32Inst I{m->d_tets, m->d_geo32, (const float*)v, (const float*)l.u0t, (float*)l.vt,
-                    (const float*)l.tau, (const float*)l.t0, pr->d_dmask, (float*)hv,
-                    phys_of<float>(pr, true), m->E, m->V, N};
+    J32Inst I{m->d_tets, m->d_geo32, (const float*)v, (const float*)l.u0t, (float*)l.vt,
+              (const float*)l.tau, (const float*)l.t0, pr->d_dmask, (float*)hv,
+              phys_of<float>(pr, true), m->E, m->V, N};
+    if (mode == MODE_JVP_EXACT) {
+      if (!pr->d_dT) TS_TRY(dalloc(&pr->d_dT, (size_t)m->E * 12 * pr->C));
+      if (launch_dtau<N>(m->d_tets, m->d_geo32, (const float*)l.u0, (const float*)v, pr->d_dmask, pr->d_eig,
+                         (const float*)l.l0, pr->d_dT, m->E, st))
+        return fail(TS_ERR_CUDA, "tau derivative kernel launch failed");
+      I.dT = pr->d_dT;
+    }
     int rc = launch_jvp32<N>(mode, I, st, pr->sev[3], pr->sev[4]);
     if (rc) return fail(TS_ERR_CUDA, "FP32 tangent kernel launch failed");
     pr->sev_jvp = true;
@@ -1007,6 +1054,8 @@ void ts_problem_free(ts_problem* pr) {
   dfree(pr->d_D);
   dfree(pr->d_t);
   dfree(pr->d_binv);
+  dfree(pr->d_eig);
+  dfree(pr->d_dT);
   dfree(pr->d_hasm);
   dfree(pr->d_r32);
   dfree(pr->d_z32);
@@ -1028,6 +1077,12 @@ int ts_problem_option(ts_problem* pr, int key, int value) {
     if (value != TS_TAU64_REFINE && value != TS_TAU64_DOUBLEFLOAT && value != TS_TAU64_JACOBI)
       return fail(TS_ERR_ARG, "unknown TS_OPT_TAU64 value");
     pr->tau64 = value;
+    return 0;
+  }
+  if (key == TS_OPT_ELEMENT64) {
+    if (value != TS_ELEMENT64_NATIVE && value != TS_ELEMENT64_DOUBLEFLOAT)
+      return fail(TS_ERR_ARG, "unknown TS_OPT_ELEMENT64 value");
+    pr->elem64 = value;
     return 0;
   }
   if (key == TS_OPT_FP32_TANGENT) {
@@ -1079,7 +1134,7 @@ std::complex<double> inlet_mode_value(int profile, int n, double r, double R, st
 
 extern "C" {
 
-int ts_set_inlet(ts_problem* pr, int tag, const double* Qn_host, int profile) {
+int ts_set_inlet(ts_problem* pr, int tag, const double* Qn_host, int profile, const double* geometry_host) {
   if (!pr || !Qn_host) return fail(TS_ERR_ARG, "ts_set_inlet: NULL argument");
   if (profile != TS_PROFILE_PARABOLIC && profile != TS_PROFILE_WOMERSLEY)
     return fail(TS_ERR_ARG, "ts_set_inlet: unknown profile");
@@ -1114,54 +1169,52 @@ int ts_set_inlet(ts_problem* pr, int tag, const double* Qn_host, int profile) {
   in.tag = tag;
   in.profile = profile;
   for (int i = 0; i < 3; ++i) in.dir[i] = -nrm[i] / nl;
-  // orthonormal in-plane basis e1, e2
   const double* d = in.dir;
-  double e1[3];
-  if (std::fabs(d[0]) < 0.9) { e1[0] = 0; e1[1] = -d[2]; e1[2] = d[1]; }
-  else { e1[0] = d[2]; e1[1] = 0; e1[2] = -d[0]; }
-  const double l1 = std::sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
-  for (double& x : e1) x /= l1;
-  const double e2[3] = {d[1] * e1[2] - d[2] * e1[1], d[2] * e1[0] - d[0] * e1[2], d[0] * e1[1] - d[1] * e1[0]};
-  // circle through the rim nodes (algebraic least-squares fit, Kasa 1976):
-  // minimise sum (a^2 + b^2 + D a + E b + F)^2 over the in-plane coordinates (a, b)
-  double S[3][3] = {{0}}, rhs[3] = {0, 0, 0}, zsum = 0;
+  // centre: the area-weighted centroid of the tag's triangles; radius: the
+  // largest distance of a rim node from the axis through the centre
+  double cen[3] = {0, 0, 0}, atot = 0;
+  for (int64_t f = 0; f < m->F; ++f) {
+    if (m->btag[f] != tag) continue;
+    const int32_t* t = &m->bfaces[3 * f];
+    const double *pa = &m->xyz[3 * t[0]], *pb = &m->xyz[3 * t[1]], *pc = &m->xyz[3 * t[2]];
+    double u[3], v[3];
+    for (int i = 0; i < 3; ++i) {
+      u[i] = pb[i] - pa[i];
+      v[i] = pc[i] - pa[i];
+    }
+    const double cx = u[1] * v[2] - u[2] * v[1], cy = u[2] * v[0] - u[0] * v[2], cz = u[0] * v[1] - u[1] * v[0];
+    const double ar = 0.5 * std::sqrt(cx * cx + cy * cy + cz * cz);
+    for (int i = 0; i < 3; ++i) cen[i] += ar * (pa[i] + pb[i] + pc[i]) / 3.0;
+    atot += ar;
+  }
+  for (int i = 0; i < 3; ++i) in.centre[i] = cen[i] / atot;
   int n_rim = 0;
+  double rmax = 0;
   for (int64_t v = 0; v < m->V; ++v) {
     if (!on_tag[v]) continue;
     in.nodes.push_back((int32_t)v);
     if (!on_other[v]) continue;
     const double* x = &m->xyz[3 * v];
-    const double a = x[0] * e1[0] + x[1] * e1[1] + x[2] * e1[2];
-    const double b = x[0] * e2[0] + x[1] * e2[1] + x[2] * e2[2];
-    zsum += x[0] * d[0] + x[1] * d[1] + x[2] * d[2];
-    const double row[3] = {a, b, 1.0}, z = -(a * a + b * b);
-    for (int i = 0; i < 3; ++i) {
-      rhs[i] += row[i] * z;
-      for (int j = 0; j < 3; ++j) S[i][j] += row[i] * row[j];
-    }
+    double rel[3], ax = 0, r2 = 0;
+    for (int i = 0; i < 3; ++i) rel[i] = x[i] - in.centre[i];
+    for (int i = 0; i < 3; ++i) ax += rel[i] * d[i];
+    for (int i = 0; i < 3; ++i) r2 += (rel[i] - ax * d[i]) * (rel[i] - ax * d[i]);
+    rmax = std::max(rmax, std::sqrt(r2));
     ++n_rim;
   }
-  if (n_rim < 3) return fail(TS_ERR_ARG, "ts_set_inlet: the tag's rim (nodes shared with other tags) has < 3 nodes");
-  // 3x3 solve by Cramer's rule
-  auto det3 = [](double A[3][3]) {
-    return A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
-           A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
-  };
-  const double dS = det3(S);
-  if (!(std::fabs(dS) > 0)) return fail(TS_ERR_ARG, "ts_set_inlet: degenerate inlet rim");
-  double sol[3];
-  for (int c = 0; c < 3; ++c) {
-    double T[3][3];
-    for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j) T[i][j] = j == c ? rhs[i] : S[i][j];
-    sol[c] = det3(T) / dS;
+  if (n_rim < 3 || !(rmax > 0)) return fail(TS_ERR_ARG, "ts_set_inlet: the tag's rim (nodes shared with other tags) has < 3 nodes");
+  in.R = rmax;
+  if (geometry_host) {
+    double dl = 0;
+    for (int i = 0; i < 3; ++i) dl += geometry_host[3 + i] * geometry_host[3 + i];
+    dl = std::sqrt(dl);
+    if (!(dl > 0) || !(geometry_host[6] > 0)) return fail(TS_ERR_ARG, "ts_set_inlet: bad inlet geometry");
+    for (int i = 0; i < 3; ++i) {
+      in.centre[i] = geometry_host[i];
+      in.dir[i] = geometry_host[3 + i] / dl;
+    }
+    in.R = geometry_host[6];
   }
-  const double ca = -0.5 * sol[0], cb = -0.5 * sol[1];
-  const double R2 = ca * ca + cb * cb - sol[2];
-  if (!(R2 > 0)) return fail(TS_ERR_ARG, "ts_set_inlet: inlet rim is not a circle");
-  in.R = std::sqrt(R2);
-  const double zc = zsum / n_rim;
-  for (int i = 0; i < 3; ++i) in.centre[i] = ca * e1[i] + cb * e2[i] + zc * d[i];
   // Dirichlet velocity modes: profile x flow-rate coefficient along the inflow direction
   const double nu = pr->p.mu / pr->p.rho;
   in.vals.assign(in.nodes.size() * 3 * C, 0.0);
@@ -1373,6 +1426,141 @@ int ts_jvp(ts_problem* pr, const void* v, void* hv, int precision, void* stream)
   if (v == hv) return fail(TS_ERR_ARG, "ts_jvp: v and Hv alias");
   TS_TRY(sync_dmask(pr));
   return jvp_any(pr, v, hv, precision, (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ tracer (eq. 3D-weak)
+
+struct ts_tracer {
+  const ts_mesh* mesh = nullptr;
+  int N = 0, C = 0, NTP = 0;
+  double kappa = 0, omega = 0, C_I = 3;
+  std::vector<uint8_t> dmask;
+  uint8_t* d_dmask = nullptr;
+  bool dirty = true;
+  double *a4_64 = nullptr, *tau64 = nullptr, *dft64 = nullptr;
+  float *a4_32 = nullptr, *tau32 = nullptr, *dft32 = nullptr;
+  unsigned* d_counter = nullptr;
+};
+
+namespace {
+
+template <typename T>
+T*& tr_a4(ts_tracer* t);
+template <>
+double*& tr_a4<double>(ts_tracer* t) { return t->a4_64; }
+template <>
+float*& tr_a4<float>(ts_tracer* t) { return t->a4_32; }
+template <typename T>
+T*& tr_tau(ts_tracer* t);
+template <>
+double*& tr_tau<double>(ts_tracer* t) { return t->tau64; }
+template <>
+float*& tr_tau<float>(ts_tracer* t) { return t->tau32; }
+template <typename T>
+T*& tr_dft(ts_tracer* t);
+template <>
+double*& tr_dft<double>(ts_tracer* t) { return t->dft64; }
+template <>
+float*& tr_dft<float>(ts_tracer* t) { return t->dft32; }
+
+template <typename T, int N>
+int tracer_residual_impl(ts_tracer* tr, const T* a, const T* phi, T* r, cudaStream_t st) {
+  const ts_mesh* m = tr->mesh;
+  T*& a4 = tr_a4<T>(tr);
+  T*& tau = tr_tau<T>(tr);
+  T*& dft = tr_dft<T>(tr);
+  if (!a4) TS_TRY(dalloc(&a4, (size_t)m->V * 4 * tr->C));
+  if (!tau) TS_TRY(dalloc(&tau, (size_t)m->E * 4 * tr->NTP));
+  if (!dft) {
+    std::vector<double> tab;
+    dft_tables(N, tab);
+    std::vector<T> tt(tab.begin(), tab.end());
+    TS_TRY(dalloc(&dft, tt.size()));
+    TS_CUDA(cudaMemcpy(dft, tt.data(), tt.size() * sizeof(T), cudaMemcpyHostToDevice));
+  }
+  if (tr->dirty) {
+    TS_CUDA(cudaMemcpy(tr->d_dmask, tr->dmask.data(), tr->dmask.size(), cudaMemcpyHostToDevice));
+    tr->dirty = false;
+  }
+  if (launch_repack_velocity<T>(a, a4, m->V, tr->C, st)) return fail(TS_ERR_CUDA, "repack kernel launch failed");
+  int rc;
+  if constexpr (sizeof(T) == 8)
+    rc = launch_tau_dd<N>(m->d_tets, m->d_geo64, a4, m->E, tau, tr->kappa, tr->C_I, tr->d_counter, st);
+  else
+    rc = launch_tau<float, N>(m->d_tets, m->d_geo32, a4, m->E, tau, (float)tr->kappa, (float)tr->C_I,
+                              tr->d_counter, st);
+  if (rc) return fail(TS_ERR_CUDA, "tau kernel launch failed");
+  TS_CUDA(cudaMemsetAsync(r, 0, (size_t)m->V * tr->C * sizeof(T), st));
+  for (size_t c = 0; c + 1 < m->colour_off.size(); ++c)
+    if (launch_tracer<T, N>(m->d_tets, geo_of<T>(m), a4, phi, tau, tr->d_dmask, r, dft, tr->kappa, tr->omega,
+                            m->colour_off[c], m->colour_off[c + 1], st))
+      return fail(TS_ERR_CUDA, "tracer kernel launch failed");
+  return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ts_tracer_create(const ts_mesh* mesh, int N, double kappa, double omega, double C_I, ts_tracer** out) {
+  if (!out || !mesh) return fail(TS_ERR_ARG, "ts_tracer_create: NULL argument");
+  *out = nullptr;
+  if (!n_supported(N)) return fail(TS_ERR_UNSUPPORTED, "ts_tracer_create: N not compiled");
+  if (!(kappa > 0) || !(omega >= 0) || !(C_I > 0))
+    return fail(TS_ERR_ARG, "ts_tracer_create: kappa and C_I must be positive, omega >= 0");
+  ts_tracer* t = new ts_tracer();
+  t->mesh = mesh;
+  t->N = N;
+  t->C = 2 * N;
+  const int nm = 2 * N - 1;
+  t->NTP = ((nm * (nm + 1) / 2) + 3) & ~3;
+  t->kappa = kappa;
+  t->omega = omega;
+  t->C_I = C_I;
+  t->dmask.assign(mesh->V, 0);
+  if (dalloc(&t->d_dmask, (size_t)mesh->V) || dalloc(&t->d_counter, 1)) {
+    ts_tracer_free(t);
+    return TS_ERR_OOM;
+  }
+  cudaMemset(t->d_counter, 0, sizeof(unsigned));
+  *out = t;
+  return 0;
+}
+
+void ts_tracer_free(ts_tracer* t) {
+  if (!t) return;
+  dfree(t->d_dmask);
+  dfree(t->d_counter);
+  dfree(t->a4_64);
+  dfree(t->tau64);
+  dfree(t->dft64);
+  dfree(t->a4_32);
+  dfree(t->tau32);
+  dfree(t->dft32);
+  delete t;
+}
+
+int ts_tracer_set_dirichlet(ts_tracer* t, int tag) {
+  if (!t) return fail(TS_ERR_ARG, "NULL tracer");
+  const ts_mesh* m = t->mesh;
+  for (int64_t f = 0; f < m->F; ++f)
+    if (m->btag[f] == tag)
+      for (int k = 0; k < 3; ++k) t->dmask[m->bfaces[3 * f + k]] = 1;
+  t->dirty = true;
+  return 0;
+}
+
+int ts_tracer_residual(ts_tracer* t, const void* a, const void* phi, void* r, int precision, void* stream) {
+  if (!t || !a || !phi || !r) return fail(TS_ERR_ARG, "ts_tracer_residual: NULL argument");
+  if (precision != 32 && precision != 64) return fail(TS_ERR_ARG, "precision must be 32 or 64");
+  if (phi == r || a == r) return fail(TS_ERR_ARG, "ts_tracer_residual: r aliases an input");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (precision == 64) {
+    TS_DISPATCH(t->N, (tracer_residual_impl<double, NN>(t, (const double*)a, (const double*)phi, (double*)r, st)));
+  }
+  TS_DISPATCH(t->N, (tracer_residual_impl<float, NN>(t, (const float*)a, (const float*)phi, (float*)r, st)));
 }
 
 }  // extern "C"

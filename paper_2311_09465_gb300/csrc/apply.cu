@@ -24,6 +24,7 @@
 // node, so each warp adds its 4x4xC results to the nodes without atomics;
 // the host launches the colours in order (deterministic).
 #include "common.cuh"
+#include "ddfloat.cuh"
 #include "kernels.h"
 
 namespace ts {
@@ -63,6 +64,10 @@ struct ApplyLayout {
   static constexpr int WARP = (END + 3) & ~3;
 };
 
+__device__ __forceinline__ float mad(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double mad(double a, double b, double c) { return ::fma(a, b, c); }
+__device__ __forceinline__ ddv mad(ddv a, ddv b, ddv c) { return ddv(dd_fma(a.v, b.v, c.v)); }
+
 // out[b*os + r] = sum_c M[r*ld + c] in[b*is + c]
 template <typename T, int R, int CN>
 __device__ __forceinline__ void warp_bmv(const T* __restrict__ M, int ld, const T* in, int is,
@@ -73,7 +78,7 @@ __device__ __forceinline__ void warp_bmv(const T* __restrict__ M, int ld, const 
     const T* x = in + b * is;
     T acc = 0;
 #pragma unroll
-    for (int c = 0; c < CN; ++c) acc = fma(mr[c], x[c], acc);
+    for (int c = 0; c < CN; ++c) acc = mad(mr[c], x[c], acc);
     out[b * os + r] = acc;
   }
 }
@@ -85,12 +90,28 @@ __device__ __forceinline__ T omega_apply(const T* x, int c, T omega) {
   return (c & 1) ? T(n) * omega * x[c - 1] : -T(n) * omega * x[c + 1];
 }
 
-template <typename T, int N, int MODE>
+template <>
+struct Real<ddv> {
+  static __device__ __forceinline__ ddv sqrt2() { return ddv(dd{1.41421353816986083984375f, 2.4203234101944225e-08f}); }
+  static __device__ __forceinline__ ddv inv_sqrt2() { return ddv(dd{0.707106769084930419921875f, 1.2101617050972112e-08f}); }
+};
+template <typename T>
+__device__ __forceinline__ T sqrt2_of() { return Real<T>::SQRT2; }
+template <>
+__device__ __forceinline__ ddv sqrt2_of<ddv>() { return Real<ddv>::sqrt2(); }
+template <typename T>
+__device__ __forceinline__ T inv_sqrt2_of() { return Real<T>::INV_SQRT2; }
+template <>
+__device__ __forceinline__ ddv inv_sqrt2_of<ddv>() { return Real<ddv>::inv_sqrt2(); }
+
+// T: arithmetic type (float, double, or the double-float ddv); S: storage type
+// of every global array (T, or double for ddv)
+template <typename T, int N, int MODE, typename S = T>
 __global__ void __launch_bounds__(128)
-    apply_kernel(const int4* __restrict__ tets, const T* __restrict__ geo,
-                 const T* __restrict__ v, const T* __restrict__ u0, const T* __restrict__ tau,
-                 T* __restrict__ t0cache, const uint8_t* __restrict__ dmask, T* __restrict__ out,
-                 const T* __restrict__ dft, Phys<T> ph, int64_t e0, int64_t e1) {
+    apply_kernel(const int4* __restrict__ tets, const S* __restrict__ geo,
+                 const S* __restrict__ v, const S* __restrict__ u0, const S* __restrict__ tau,
+                 S* __restrict__ t0cache, const uint8_t* __restrict__ dmask, S* __restrict__ out,
+                 const S* __restrict__ dft, Phys<T> ph, int64_t e0, int64_t e1, S* __restrict__ l0cache) {
   using D = Dims<N>;
   using L = ApplyLayout<N, MODE>;
   constexpr int C = D::C, K = D::K, NM = D::NM, NT = D::NT, NTP = D::NT_PAD;
@@ -102,11 +123,11 @@ __global__ void __launch_bounds__(128)
   T* sI = sF + K * L::LDF;                  // inverse DFT [C][LDI]
   for (int t = threadIdx.x; t < K * C; t += blockDim.x) {
     const int kk = t / C, c = t - kk * C;
-    sF[kk * L::LDF + c] = dft[t];
+    sF[kk * L::LDF + c] = T(dft[t]);
   }
   for (int t = threadIdx.x; t < C * K; t += blockDim.x) {
     const int c = t / K, kk = t - c * K;
-    sI[c * L::LDI + kk] = dft[K * C + t];
+    sI[c * L::LDI + kk] = T(dft[K * C + t]);
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -139,11 +160,11 @@ __global__ void __launch_bounds__(128)
        e += (int64_t)gridDim.x * wpb) {
     const int4 nd = tets[e];
     const int node[4] = {nd.x, nd.y, nd.z, nd.w};
-    if (lane < GEO_STRIDE) sg[lane] = geo[e * GEO_STRIDE + lane];
+    if (lane < GEO_STRIDE) sg[lane] = T(geo[e * GEO_STRIDE + lane]);
     for (int t = lane; t < 16 * C; t += 32) {
       const int a = t / (4 * C), r = t - a * 4 * C;
       const int f = r / C, c = r - f * C;
-      T val = v[(int64_t)node[a] * 4 * C + r];
+      T val = T(v[(int64_t)node[a] * 4 * C + r]);
       if (c == 1) val = T(0);
       if (!RES && f < 3 && dmask[node[a]]) val = T(0);
       sv[t] = val;
@@ -151,12 +172,12 @@ __global__ void __launch_bounds__(128)
     for (int t = lane; t < 12 * C; t += 32) {
       const int a = t / (3 * C), r = t - a * 3 * C;
       const int c = r % C;
-      T val = u0[(int64_t)node[a] * 4 * C + r];
+      T val = T(u0[(int64_t)node[a] * 4 * C + r]);
       su[t] = (c == 1) ? T(0) : val;
     }
     // tau: packed symmetric (orthonormal basis) -> full matrix in storage scaling
     {
-      const T* tp = tau + e * 4 * NTP;
+      const S* tp = tau + e * 4 * NTP;
       for (int t = lane; t < 4 * NTP; t += 32) {
         const int q = t / NTP, p = t - q * NTP;
         if (p >= NT) continue;
@@ -166,17 +187,17 @@ __global__ void __launch_bounds__(128)
           ++r;
         }
         const int s = r + rem;
-        const T val = tp[t];
+        const T val = T(tp[t]);
         // T_s[r] = (1/d_r) sum_k tau[r][k] d_k L_s[k], d_0 = 1, d_k = sqrt2
-        const T drs = (r == 0 && s > 0) ? Real<T>::SQRT2 : T(1);
-        const T dsr = (r == 0 && s > 0) ? Real<T>::INV_SQRT2 : T(1);
+        const T drs = (r == 0 && s > 0) ? sqrt2_of<T>() : T(1);
+        const T dsr = (r == 0 && s > 0) ? inv_sqrt2_of<T>() : T(1);
         st[q * NM * NM + r * NM + s] = val * drs;
         st[q * NM * NM + s * NM + r] = val * dsr;
       }
     }
     if (LINA) {
-      const T* tp = t0cache + e * 12 * C;
-      for (int t = lane; t < 12 * C; t += 32) t0[t] = tp[t];
+      const S* tp = t0cache + e * 12 * C;
+      for (int t = lane; t < 12 * C; t += 32) t0[t] = T(tp[t]);
     }
     __syncwarp();
     const T vol = sg[GEO_VOL];
@@ -266,15 +287,21 @@ __global__ void __launch_bounds__(128)
       }
       tq[qi * C + stor_of(r)] = acc;
       if (PAPER) tc[qi * C + stor_of(r)] = accp;
+      // the strong residual itself (the exact tangent's tau derivative acts on it)
+      if (RES && l0cache) {
+        const int cs = stor_of(r);
+        l0cache[(e * 12 + qi) * C + cs] = static_cast<S>(lu[cs] + lp[cs]);
+      }
     }
     for (int qi = lane; qi < 12; qi += 32) {
       tq[qi * C + 1] = T(0);
       if (PAPER) tc[qi * C + 1] = T(0);
+      if (RES && l0cache) l0cache[(e * 12 + qi) * C + 1] = S(0);
     }
     __syncwarp();
     if (RES) {
-      T* tp = t0cache + e * 12 * C;
-      for (int t = lane; t < 12 * C; t += 32) tp[t] = tq[t];
+      S* tp = t0cache + e * 12 * C;
+      for (int t = lane; t < 12 * C; t += 32) tp[t] = static_cast<S>(tq[t]);
     }
     // ---- phase 7: T (and T0) to samples
     warp_bmv<T, K, C>(sF, L::LDF, tq, C, ct, K, 12, lane);
@@ -346,30 +373,31 @@ __global__ void __launch_bounds__(128)
       const int f = r / C, c = r - f * C;
       if (c == 1) continue;
       if (f < 3 && dmask[node[a]]) continue;
-      T* dst = out + (int64_t)node[a] * 4 * C + r;
-      *dst += so[t];
+      S* dst = out + (int64_t)node[a] * 4 * C + r;
+      *dst += static_cast<S>(so[t]);
     }
     __syncwarp();
   }
 }
 
-template <typename T, int N, int MODE>
-static int launch_mode(const int4* tets, const T* geo, const T* v, const T* u0, const T* tau,
-                       T* t0cache, const uint8_t* dmask, T* out, const T* dft, Phys<T> ph,
-                       int64_t e0, int64_t e1, cudaStream_t st) {
+template <typename T, int N, int MODE, typename S = T>
+static int launch_mode(const int4* tets, const S* geo, const S* v, const S* u0, const S* tau,
+                       S* t0cache, const uint8_t* dmask, S* out, const S* dft, Phys<T> ph,
+                       int64_t e0, int64_t e1, cudaStream_t st, S* l0cache = nullptr) {
   using L = ApplyLayout<N, MODE>;
+  static_assert(sizeof(T) == sizeof(S) || sizeof(T) == 8, "workspace sized by T");
   if (e1 <= e0) return 0;
   int warps = 4;
   while (warps > 1 && (size_t)(L::TABLES + warps * L::WARP) * sizeof(T) > 200 * 1024) --warps;
   const size_t smem = (size_t)(L::TABLES + warps * L::WARP) * sizeof(T);
   if (smem > 227 * 1024) return -6;
-  cudaFuncSetAttribute(apply_kernel<T, N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(apply_kernel<T, N, MODE, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)smem);
   int64_t blocks = (e1 - e0 + warps - 1) / warps;
   if (blocks > 152 * 32) blocks = 152 * 32;
   count_launches(1);
-  apply_kernel<T, N, MODE><<<(int)blocks, warps * 32, smem, st>>>(tets, geo, v, u0, tau, t0cache,
-                                                                  dmask, out, dft, ph, e0, e1);
+  apply_kernel<T, N, MODE, S><<<(int)blocks, warps * 32, smem, st>>>(tets, geo, v, u0, tau, t0cache,
+                                                                     dmask, out, dft, ph, e0, e1, l0cache);
   return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
@@ -392,11 +420,11 @@ int preload_apply_residual() {
 template <typename T, int N>
 int launch_apply(int mode, const int4* tets, const T* geo, const T* v, const T* u0,
                  const T* tau, T* t0cache, const uint8_t* dmask, T* out, const T* dft,
-                 Phys<T> ph, int64_t e0, int64_t e1, cudaStream_t st) {
+                 Phys<T> ph, int64_t e0, int64_t e1, cudaStream_t st, T* l0cache) {
   switch (mode) {
     case MODE_RESIDUAL:
       return launch_mode<T, N, MODE_RESIDUAL>(tets, geo, v, u0, tau, t0cache, dmask, out, dft,
-                                              ph, e0, e1, st);
+                                              ph, e0, e1, st, l0cache);
     case MODE_JVP_PAPER:
       return launch_mode<T, N, MODE_JVP_PAPER>(tets, geo, v, u0, tau, t0cache, dmask, out, dft,
                                                ph, e0, e1, st);
@@ -409,6 +437,275 @@ int launch_apply(int mode, const int4* tets, const T* geo, const T* v, const T* 
   }
   return -1;
 }
+
+// The FP64 operator with its arithmetic in double-float (FP64 storage)
+template <int N>
+int launch_apply_dd(int mode, const int4* tets, const double* geo, const double* v, const double* u0,
+                    const double* tau, double* t0cache, const uint8_t* dmask, double* out, const double* dft,
+                    Phys<double> p, int64_t e0, int64_t e1, cudaStream_t st, double* l0cache) {
+  Phys<ddv> ph{ddv(p.rho), ddv(p.mu), ddv(p.omega), ddv(p.nu), ddv(p.C_I), ddv(p.mass_coef)};
+  switch (mode) {
+    case MODE_RESIDUAL:
+      return launch_mode<ddv, N, MODE_RESIDUAL, double>(tets, geo, v, u0, tau, t0cache, dmask, out, dft,
+                                                        ph, e0, e1, st, l0cache);
+    case MODE_JVP_PAPER:
+      return launch_mode<ddv, N, MODE_JVP_PAPER, double>(tets, geo, v, u0, tau, t0cache, dmask, out, dft,
+                                                         ph, e0, e1, st);
+    case MODE_JVP_FROZEN:
+      return launch_mode<ddv, N, MODE_JVP_FROZEN, double>(tets, geo, v, u0, tau, t0cache, dmask, out, dft,
+                                                          ph, e0, e1, st);
+    case MODE_JVP_LIN_A:
+      return launch_mode<ddv, N, MODE_JVP_LIN_A, double>(tets, geo, v, u0, tau, t0cache, dmask, out, dft,
+                                                         ph, e0, e1, st);
+  }
+  return -1;
+}
+
+// ---------------------------------------------------------------- tracer
+// Time-spectral GLS convection-diffusion of a scalar phi (eq. 3D-weak with
+// eq. 3D-weak-def, section 2.2) advected by a given velocity a: per element
+// and quadrature point (weights V/4)
+//   res  = Omega phi + A_j dphi/dx_j          (A_j = A(a_j), eq. phi-def)
+//   T    = tau res                            (tau of eq. 3D-tau with kappa)
+//   r_a += w [N_a res - N_a Omega T + dN_a/dx_j A_j T] + kappa V dN_a/dx_j dphi/dx_j
+// The products A_j x are formed on K = 3N - 2 time samples, as in the flow
+// operator; the SUPG sum sum_q w A_j T is transformed once per element.
+template <int N>
+struct TracerLayout {
+  using D = Dims<N>;
+  static constexpr int C = D::C, K = D::K, NM = D::NM;
+  static constexpr int LDF = C | 1, LDI = K | 1;
+  static constexpr int TABLES = K * LDF + C * LDI;
+  static constexpr int SG = 0;              // geometry 20 (+4)
+  static constexpr int PH = 24;             // phi at nodes [4][C]
+  static constexpr int AN = PH + 4 * C;     // a at nodes [4][3][C]
+  static constexpr int GP = AN + 12 * C;    // grad phi [3][C]
+  static constexpr int PQ = GP + 3 * C;     // phi at points [4][C]
+  static constexpr int AQ = PQ + 4 * C;     // a at points [4][3][C]
+  static constexpr int AQT = AQ + 12 * C;   // a samples [4][3][K]
+  static constexpr int GPT = AQT + 12 * K;  // grad phi samples [3][K], later W samples
+  static constexpr int CT = GPT + 3 * K;    // c samples [4][K], later T samples
+  static constexpr int RES = CT + 4 * K;    // res modes [4][C]
+  static constexpr int TQ = RES + 4 * C;    // T modes [4][C]
+  static constexpr int WM = TQ + 4 * C;     // W modes [3][C]
+  static constexpr int TAU = WM + 3 * C;    // tau [4][NM][NM] (storage scaling)
+  static constexpr int OUT = TAU + 4 * NM * NM;   // [4][C]
+  static constexpr int WARP = (OUT + 4 * C + 3) & ~3;
+};
+
+template <typename T, int N, typename S = T>
+__global__ void __launch_bounds__(128)
+    tracer_kernel(const int4* __restrict__ tets, const S* __restrict__ geo, const S* __restrict__ a4,
+                  const S* __restrict__ phi, const S* __restrict__ tau, const uint8_t* __restrict__ dmask,
+                  S* __restrict__ out, const S* __restrict__ dft, T kappa, T omega, int64_t e0, int64_t e1) {
+  using D = Dims<N>;
+  using L = TracerLayout<N>;
+  constexpr int C = D::C, K = D::K, NM = D::NM, NT = D::NT, NTP = D::NT_PAD;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sF = reinterpret_cast<T*>(smem_raw);
+  T* sI = sF + K * L::LDF;
+  for (int t = threadIdx.x; t < K * C; t += blockDim.x) {
+    const int kk = t / C, c = t - kk * C;
+    sF[kk * L::LDF + c] = T(dft[t]);
+  }
+  for (int t = threadIdx.x; t < C * K; t += blockDim.x) {
+    const int c = t / K, kk = t - c * K;
+    sI[c * L::LDI + kk] = T(dft[K * C + t]);
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T* ws = sF + L::TABLES + warp * L::WARP;
+  T* sg = ws + L::SG;
+  T* ph = ws + L::PH;
+  T* an = ws + L::AN;
+  T* gp = ws + L::GP;
+  T* pq = ws + L::PQ;
+  T* aq = ws + L::AQ;
+  T* aqt = ws + L::AQT;
+  T* gpt = ws + L::GPT;
+  T* ct = ws + L::CT;
+  T* res = ws + L::RES;
+  T* tq = ws + L::TQ;
+  T* wm = ws + L::WM;
+  T* st = ws + L::TAU;
+  T* so = ws + L::OUT;
+  const int wpb = blockDim.x >> 5;
+  for (int64_t e = e0 + (int64_t)blockIdx.x * wpb + warp; e < e1; e += (int64_t)gridDim.x * wpb) {
+    const int4 nd = tets[e];
+    const int node[4] = {nd.x, nd.y, nd.z, nd.w};
+    if (lane < GEO_STRIDE) sg[lane] = T(geo[e * GEO_STRIDE + lane]);
+    for (int t = lane; t < 4 * C; t += 32) {
+      const int a = t / C, c = t - a * C;
+      ph[t] = c == 1 ? T(0) : T(phi[(int64_t)node[a] * C + c]);
+    }
+    for (int t = lane; t < 12 * C; t += 32) {
+      const int a = t / (3 * C), r = t - a * 3 * C;
+      const int c = r % C;
+      an[t] = c == 1 ? T(0) : T(a4[(int64_t)node[a] * 4 * C + r]);
+    }
+    {
+      const S* tp = tau + e * 4 * NTP;
+      for (int t = lane; t < 4 * NTP; t += 32) {
+        const int q = t / NTP, p = t - q * NTP;
+        if (p >= NT) continue;
+        int r = 0, rem = p;
+        while (rem >= NM - r) {
+          rem -= NM - r;
+          ++r;
+        }
+        const int s2 = r + rem;
+        const T val = T(tp[t]);
+        const T drs = (r == 0 && s2 > 0) ? sqrt2_of<T>() : T(1);
+        const T dsr = (r == 0 && s2 > 0) ? inv_sqrt2_of<T>() : T(1);
+        st[q * NM * NM + r * NM + s2] = val * drs;
+        st[q * NM * NM + s2 * NM + r] = val * dsr;
+      }
+    }
+    __syncwarp();
+    const T vol = sg[GEO_VOL], w4 = T(0.25) * vol;
+    for (int t = lane; t < 3 * C; t += 32) {
+      const int j = t / C, c = t - j * C;
+      T acc = 0;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) acc += sg[a * 3 + j] * ph[a * C + c];
+      gp[t] = acc;
+    }
+    for (int t = lane; t < 4 * C; t += 32) {
+      const int q = t / C, c = t - q * C;
+      T acc = 0;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) acc += T(qp_bary(q, a)) * ph[a * C + c];
+      pq[t] = acc;
+    }
+    for (int t = lane; t < 12 * C; t += 32) {
+      const int q = t / (3 * C), r = t - q * 3 * C;
+      T acc = 0;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) acc += T(qp_bary(q, a)) * an[a * 3 * C + r];
+      aq[t] = acc;
+    }
+    __syncwarp();
+    warp_bmv<T, K, C>(sF, L::LDF, aq, C, aqt, K, 12, lane);
+    warp_bmv<T, K, C>(sF, L::LDF, gp, C, gpt, K, 3, lane);
+    __syncwarp();
+    // convective product on samples c(q, t) = sum_j a_j(q, t) dphi/dx_j(t)
+    for (int t = lane; t < 4 * K; t += 32) {
+      const int q = t / K, kk = t - q * K;
+      T acc = 0;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) acc += aqt[(q * 3 + j) * K + kk] * gpt[j * K + kk];
+      ct[t] = acc;
+    }
+    __syncwarp();
+    warp_bmv<T, C, K>(sI, L::LDI, ct, K, res, C, 4, lane);
+    __syncwarp();
+    for (int t = lane; t < 4 * C; t += 32) {
+      const int c = t % C;
+      res[t] = c == 1 ? T(0) : omega_apply(pq + (t - c), c, omega) + res[t];
+    }
+    __syncwarp();
+    // T = tau res (storage coordinates)
+    for (int t = lane; t < 4 * NM; t += 32) {
+      const int q = t / NM, r = t - q * NM;
+      const T* tr = st + q * NM * NM + r * NM;
+      const T* rq = res + q * C;
+      T acc = 0;
+#pragma unroll
+      for (int kk = 0; kk < NM; ++kk) acc = mad(tr[kk], rq[stor_of(kk)], acc);
+      tq[q * C + stor_of(r)] = acc;
+    }
+    for (int q = lane; q < 4; q += 32) tq[q * C + 1] = T(0);
+    __syncwarp();
+    warp_bmv<T, K, C>(sF, L::LDF, tq, C, ct, K, 4, lane);
+    __syncwarp();
+    // SUPG sums on samples W_j(t) = sum_q a_j(q, t) T(q, t)
+    for (int t = lane; t < 3 * K; t += 32) {
+      const int j = t / K, kk = t - j * K;
+      T acc = 0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc += aqt[(q * 3 + j) * K + kk] * ct[q * K + kk];
+      gpt[t] = acc;
+    }
+    __syncwarp();
+    warp_bmv<T, C, K>(sI, L::LDI, gpt, K, wm, C, 3, lane);
+    __syncwarp();
+    for (int t = lane; t < 4 * C; t += 32) {
+      const int a = t / C, c = t - a * C;
+      T acc = 0;
+      if (c != 1) {
+        T gal = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const T lam = T(qp_bary(q, a));
+          gal += lam * (res[q * C + c] - omega_apply(tq + q * C, c, omega));
+        }
+        T supg = 0, diff = 0;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          supg += sg[a * 3 + j] * wm[j * C + c];
+          diff += sg[a * 3 + j] * gp[j * C + c];
+        }
+        acc = w4 * (gal + supg) + kappa * vol * diff;
+      }
+      so[t] = acc;
+    }
+    __syncwarp();
+    for (int t = lane; t < 4 * C; t += 32) {
+      const int a = t / C, c = t - a * C;
+      if (c == 1 || dmask[node[a]]) continue;
+      out[(int64_t)node[a] * C + c] += static_cast<S>(so[t]);
+    }
+    __syncwarp();
+  }
+}
+
+template <typename T, int N, typename S>
+static int launch_tracer_t(const int4* tets, const S* geo, const S* a4, const S* phi, const S* tau,
+                           const uint8_t* dmask, S* out, const S* dft, double kappa, double omega,
+                           int64_t e0, int64_t e1, cudaStream_t st) {
+  using L = TracerLayout<N>;
+  if (e1 <= e0) return 0;
+  int warps = 4;
+  while (warps > 1 && (size_t)(L::TABLES + warps * L::WARP) * sizeof(T) > 200 * 1024) --warps;
+  const size_t smem = (size_t)(L::TABLES + warps * L::WARP) * sizeof(T);
+  if (smem > 227 * 1024) return -6;
+  cudaFuncSetAttribute(tracer_kernel<T, N, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int64_t blocks = (e1 - e0 + warps - 1) / warps;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  count_launches(1);
+  tracer_kernel<T, N, S><<<(int)blocks, warps * 32, smem, st>>>(tets, geo, a4, phi, tau, dmask, out, dft,
+                                                                T(kappa), T(omega), e0, e1);
+  return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+
+template <typename T, int N>
+int launch_tracer(const int4* tets, const T* geo, const T* a4, const T* phi, const T* tau,
+                  const uint8_t* dmask, T* out, const T* dft, double kappa, double omega, int64_t e0,
+                  int64_t e1, cudaStream_t st) {
+  return launch_tracer_t<T, N, T>(tets, geo, a4, phi, tau, dmask, out, dft, kappa, omega, e0, e1, st);
+}
+
+// a [V][3][C] -> a4 [V][4][C] (the flow layout the tau kernels read; pressure zero)
+template <typename T>
+__global__ void repack_velocity_kernel(const T* __restrict__ a, T* __restrict__ a4, int64_t V, int C) {
+  const int64_t total = V * 4 * C;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = t / (4 * C), r = t - v * 4 * C;
+    a4[t] = r < 3 * C ? a[v * 3 * C + r] : T(0);
+  }
+}
+
+template <typename T>
+int launch_repack_velocity(const T* a, T* a4, int64_t V, int C, cudaStream_t st) {
+  if (V <= 0) return 0;
+  int64_t blocks = (V * 4 * C + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  count_launches(1);
+  repack_velocity_kernel<T><<<(int)blocks, 256, 0, st>>>(a, a4, V, C);
+  return cudaGetLastError() == cudaSuccess ? 0 : -2;
+}
+template int launch_repack_velocity<float>(const float*, float*, int64_t, int, cudaStream_t);
+template int launch_repack_velocity<double>(const double*, double*, int64_t, int, cudaStream_t);
 
 // ---------------------------------------------------------------- outlets
 // One block per call: Q_c = sum_A sum_i w_Ai v[A][i][c]; out[A][i][c] += R w_Ai Q_c.
@@ -485,10 +782,20 @@ template int launch_outlet<double>(const int32_t*, const double*, int, double, c
 #define TS_INST_APPLY(T, N)                                                                  \
   template int launch_apply<T, N>(int, const int4*, const T*, const T*, const T*, const T*, \
                                   T*, const uint8_t*, T*, const T*, Phys<T>, int64_t,        \
-                                  int64_t, cudaStream_t);
+                                  int64_t, cudaStream_t, T*);
 TS_FOR_EACH_N(TS_INST_APPLY, float)
 #define TS_INST_PRELOAD_APPLY(T, N) template int preload_apply_residual<T, N>();
 TS_FOR_EACH_N(TS_INST_PRELOAD_APPLY, float)
 TS_FOR_EACH_N(TS_INST_APPLY, double)
+#define TS_INST_APPLY_DD(T, N)                                                                         \
+  template int launch_apply_dd<N>(int, const int4*, const double*, const double*, const double*,      \
+                                  const double*, double*, const uint8_t*, double*, const double*,     \
+                                  Phys<double>, int64_t, int64_t, cudaStream_t, double*);
+TS_FOR_EACH_N(TS_INST_APPLY_DD, double)
+#define TS_INST_TRACER(T, N)                                                                        \
+  template int launch_tracer<T, N>(const int4*, const T*, const T*, const T*, const T*, const uint8_t*, \
+                                   T*, const T*, double, double, int64_t, int64_t, cudaStream_t);
+TS_FOR_EACH_N(TS_INST_TRACER, float)
+TS_FOR_EACH_N(TS_INST_TRACER, double)
 
 }  // namespace ts

@@ -34,6 +34,9 @@ struct Dims {
   static constexpr int NT = NM * (NM + 1) / 2;  // packed tau entries
   static constexpr int NT_PAD = (NT + 3) & ~3;  // per quadrature point, 16-byte multiple
   static constexpr int NP = 2 * N;              // Jacobi size (NM + 1 decoupled dummy)
+  // eigenpair cache per point: eigenvectors [NM][NM] (column j = vector j,
+  // orthonormal basis) then eigenvalues [NM], padded to a 16-byte multiple
+  static constexpr int EIG = (NM * NM + NM + 3) & ~3;
 };
 
 // barycentric coordinates of the symmetric degree-2 rule (weights V/4)
@@ -66,12 +69,15 @@ struct Real<double> {
   static constexpr double INV_SQRT2 = 0.70710678118654752;
 };
 
+struct ddv;   // double-float value type (ddfloat.cuh)
+
 // kernel-side view of the problem constants
 template <typename T>
 struct Phys {
   T rho, mu, omega, nu, C_I, mass_coef;
 };
 
-enum ApplyMode { MODE_RESIDUAL = 0, MODE_JVP_PAPER = 1, MODE_JVP_FROZEN = 2, MODE_JVP_LIN_A = 3 };
+enum ApplyMode { MODE_RESIDUAL = 0, MODE_JVP_PAPER = 1, MODE_JVP_FROZEN = 2, MODE_JVP_LIN_A = 3,
+                 MODE_JVP_EXACT = 4 /* LIN_A + the derivative of tau, passed in as dT */ };
 
 }  // namespace ts

@@ -82,6 +82,19 @@ __device__ __forceinline__ dd dd_fma_ff(float a, float b, dd c) {
   return r;
 }
 
+// a * b + c for an FP32 a
+__device__ __forceinline__ dd dd_fma_fd(float a, dd b, dd c) {
+  const float p = a * b.hi;
+  float e = fmaf(a, b.hi, -p);
+  e = fmaf(a, b.lo, e);
+  float s, t;
+  two_sum(p, c.hi, s, t);
+  t += e + c.lo;
+  dd r;
+  fast_two_sum(s, t, r.hi, r.lo);
+  return r;
+}
+
 __device__ __forceinline__ dd dd_mul(dd a, dd b) {
   const float p = a.hi * b.hi;
   float e = fmaf(a.hi, b.hi, -p);
@@ -115,5 +128,28 @@ __device__ __forceinline__ dd dd_rcp(dd a) {
   fast_two_sum(y0, y0 * rem, r.hi, r.lo);
   return r;
 }
+
+// A double-float value type with arithmetic operators, so that kernels
+// templated on their arithmetic type can run in double-float: storage stays
+// FP64 (converted on load and store), every operation runs on the FP32 pipe.
+struct ddv {
+  dd v;
+  __host__ __device__ ddv() : v{0.f, 0.f} {}
+  __host__ __device__ ddv(double x) {
+    const float h = (float)x;
+    v = {h, (float)(x - (double)h)};
+  }
+  __host__ __device__ ddv(float x) : v{x, 0.f} {}
+  __host__ __device__ ddv(int x) : v{(float)x, 0.f} {}   // exact for |x| < 2^24
+  __device__ ddv(dd x) : v(x) {}
+  __host__ __device__ explicit operator double() const { return (double)v.hi + (double)v.lo; }
+};
+__device__ __forceinline__ ddv operator+(ddv a, ddv b) { return ddv(dd_add(a.v, b.v)); }
+__device__ __forceinline__ ddv operator-(ddv a) { return ddv(dd_neg(a.v)); }
+__device__ __forceinline__ ddv operator-(ddv a, ddv b) { return ddv(dd_add(a.v, dd_neg(b.v))); }
+__device__ __forceinline__ ddv operator*(ddv a, ddv b) { return ddv(dd_mul(a.v, b.v)); }
+__device__ __forceinline__ ddv operator/(ddv a, ddv b) { return ddv(dd_mul(a.v, dd_rcp(b.v))); }
+__device__ __forceinline__ ddv& operator+=(ddv& a, ddv b) { a.v = dd_add(a.v, b.v); return a; }
+__device__ __forceinline__ bool operator!=(ddv a, ddv b) { return a.v.hi != b.v.hi || a.v.lo != b.v.lo; }
 
 }  // namespace ts

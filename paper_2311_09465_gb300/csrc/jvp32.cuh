@@ -256,7 +256,7 @@ template <int N, int MODE>
 struct J32Layout {
   static constexpr int C = 2 * N, K = 3 * N - 2, NTP = Dims<N>::NT_PAD;
   static constexpr int KP = (K + 3) & ~3;   // sample rows padded to 16 bytes
-  static constexpr bool LINA = MODE == MODE_JVP_LIN_A;
+  static constexpr bool LINA = MODE == MODE_JVP_LIN_A || MODE == MODE_JVP_EXACT;
   static constexpr int STG_TAU = 0;                               // [2][4][NTP]
   static constexpr int STG_T0 = STG_TAU + EPW * 4 * NTP;          // [2][4][3][C] (LIN_A)
   static constexpr int STG = STG_T0 + (LINA ? EPW * 12 * C : 0);
@@ -453,6 +453,13 @@ __device__ __forceinline__ bool j32_pass(const J32Inst I, int64_t base, const fl
     const float* tq = stg + L::STG_TAU + (slot * 4 + q) * NTP;
     float T[C];
     tau_apply<N>(tq, Lm, T);
+    if (MODE == MODE_JVP_EXACT && live) {
+      // + d tau[v] L(u0): the derivative of tau, computed per point beforehand
+      float dt[C];
+      ld2<C>(I.dT + ((e * 4 + q) * 3 + i) * C, dt);
+#pragma unroll
+      for (int c = 0; c < C; ++c) T[c] += dt[c];
+    }
     if (PAPER) {
       float Tc[C];
       tau_apply<N>(tq, dp, Tc);
@@ -875,6 +882,7 @@ static int launch_jvp32_impl(int mode, const J32Inst& I, cudaStream_t st) {
     case MODE_JVP_PAPER: return launch_j32_mode<N, MODE_JVP_PAPER>(I, st);
     case MODE_JVP_FROZEN: return launch_j32_mode<N, MODE_JVP_FROZEN>(I, st);
     case MODE_JVP_LIN_A: return launch_j32_mode<N, MODE_JVP_LIN_A>(I, st);
+    case MODE_JVP_EXACT: return launch_j32_mode<N, MODE_JVP_EXACT>(I, st);
   }
   return -1;
 }

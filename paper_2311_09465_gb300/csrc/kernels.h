@@ -19,7 +19,7 @@ unsigned long long launches_total();
 
 template <typename T, int N>
 int launch_tau(const int4* tets, const T* geo, const T* y, int64_t n_elem, T* tau_out, T nu,
-               T C_I, unsigned* n_unconverged, cudaStream_t st);
+               T C_I, unsigned* n_unconverged, cudaStream_t st, float* eig_out = nullptr);
 
 // load a kernel into the current device's context without launching it
 // (instantiated for T = float only)
@@ -32,13 +32,13 @@ int preload_apply_residual();
 template <int N>
 int launch_tau_polish(const int4* tets, const double* geo, const double* y, int64_t n_elem,
                       double* tau_out, double nu, double C_I, unsigned* n_unconverged,
-                      cudaStream_t st);
+                      cudaStream_t st, float* eig_out = nullptr);
 
 // the same refinement in double-float arithmetic (tau_dd.cu)
 template <int N>
 int launch_tau_dd(const int4* tets, const double* geo, const double* y, int64_t n_elem,
                   double* tau_out, double nu, double C_I, unsigned* n_unconverged,
-                  cudaStream_t st);
+                  cudaStream_t st, float* eig_out = nullptr);
 
 // Backflow stabilisation on one Neumann face set (tau.cu): when y_for_matrix
 // is given, first |A_n|_- at the 3 points of every face into bneg; then
@@ -52,12 +52,29 @@ int launch_backflow(const int32_t* faces, const T* normals, const T* area, int64
 template <typename T, int N>
 int launch_apply(int mode, const int4* tets, const T* geo, const T* v, const T* u0,
                  const T* tau, T* t0cache, const uint8_t* dmask, T* out, const T* dft,
-                 Phys<T> ph, int64_t e0, int64_t e1, cudaStream_t st);
+                 Phys<T> ph, int64_t e0, int64_t e1, cudaStream_t st, T* l0cache = nullptr);
 
 // y[node][i][c] = vals[k][i][c] for the k-th listed node, velocity fields i < 3
 // (the inlet Dirichlet data of the initial guess)
 template <typename T>
 int launch_inlet_fill(const int32_t* nodes, const double* vals, int64_t n, int C, T* y, cudaStream_t st);
+
+// The same element operator on FP64 data with double-float arithmetic
+// (FP32-pipe pairs, ~48 significant bits; see ddfloat.cuh)
+template <int N>
+int launch_apply_dd(int mode, const int4* tets, const double* geo, const double* v, const double* u0,
+                    const double* tau, double* t0cache, const uint8_t* dmask, double* out, const double* dft,
+                    Phys<double> ph, int64_t e0, int64_t e1, cudaStream_t st, double* l0cache = nullptr);
+
+// Tracer residual of eq. (3D-weak) on one colour range [e0, e1) (apply.cu):
+// phi [V][C], a4 the advecting velocity in the flow layout [V][4][C], tau the
+// tracer's tau cache; out += element rows (Dirichlet rows and Im(mode 0) skipped)
+template <typename T, int N>
+int launch_tracer(const int4* tets, const T* geo, const T* a4, const T* phi, const T* tau,
+                  const uint8_t* dmask, T* out, const T* dft, double kappa, double omega, int64_t e0,
+                  int64_t e1, cudaStream_t st);
+template <typename T>
+int launch_repack_velocity(const T* a, T* a4, int64_t V, int C, cudaStream_t st);
 
 // Resistance outlets: out[A][i][c] += R w_Ai Q_c with Q_c = sum_B w_Bi v[B][i][c]
 template <typename T>
@@ -80,6 +97,7 @@ struct J32Inst {
   int64_t n_elem;
   int64_t n_nodes;
   int N;
+  const float* dT = nullptr;   // [E][4][3][C] d tau[v] L(u0) (exact tangent only)
 };
 
 // Batched LIN_A tangent products of instances with N <= J32_MAX_N in one
@@ -99,6 +117,14 @@ int j32_upload_batch(const float* host_all);
 template <int N>
 int launch_jvp32(int mode, const J32Inst& I, cudaStream_t st, cudaEvent_t e_before = nullptr,
                  cudaEvent_t e_after = nullptr);
+// d tau[v] L_i(u0) at every quadrature point (dtau.cu): the Frechet derivative of
+// tau = M^{-1/2} (eq. 3D-tau) in the direction of v, from the cached eigenpairs
+// of M (eig [E*4][EIG]) and strong residual L(u0) (l0 [E][4][3][C]);
+// dT [E][4][3][C], storage coordinates
+template <int N>
+int launch_dtau(const int4* tets, const float* geo, const float* u0, const float* v, const uint8_t* dmask,
+                const float* eig, const float* l0, float* dT, int64_t n_elem, cudaStream_t st);
+
 // u0 velocity at the nodes as time samples [V][K] float4 (x, y, z, 0)
 template <int N>
 int launch_node_samples(const float* u0, float* u0t, int64_t V, cudaStream_t st);

@@ -38,7 +38,8 @@ __global__ void __launch_bounds__(128) tau_kernel(const int4* __restrict__ tets,
                                                   const T* __restrict__ y, int64_t n_qp,
                                                   T* __restrict__ tau_out, T nu, T C_I,
                                                   int max_sweeps, T tol2,
-                                                  unsigned* __restrict__ n_unconverged) {
+                                                  unsigned* __restrict__ n_unconverged,
+                                                  float* __restrict__ eig_out) {
   using D = Dims<N>;
   using L = TauLayout<N>;
   constexpr int NP = D::NP, NM = D::NM, C = D::C, LD = L::LD, GPW = L::GPW;
@@ -127,6 +128,12 @@ __global__ void __launch_bounds__(128) tau_kernel(const int4* __restrict__ tets,
     // parallel cyclic Jacobi
     const bool converged = jacobi_group<T, N>(M, Vv, k, g, lane, live, red, max_sweeps, tol2);
     if (live && k == 0 && !converged) atomicAdd(n_unconverged, 1u);
+    // eigenpairs for the derivative of tau (exact tangent), when asked
+    if (live && eig_out) {
+      float* eo = eig_out + gq * D::EIG;
+      for (int t = k; t < NM * NM; t += N) eo[t] = (float)Vv[(t / NM) * LD + t % NM];
+      for (int j = k; j < NM; j += N) eo[NM * NM + j] = (float)M[j * LD + j];
+    }
     // tau = V diag(lambda^{-1/2}) V^T, packed upper triangle
     if (live) {
       T* out = tau_out + gq * Dims<N>::NT_PAD;
@@ -149,7 +156,7 @@ __global__ void __launch_bounds__(128) tau_kernel(const int4* __restrict__ tets,
 
 template <typename T, int N>
 int launch_tau(const int4* tets, const T* geo, const T* y, int64_t n_elem, T* tau_out, T nu,
-               T C_I, unsigned* n_unconverged, cudaStream_t st) {
+               T C_I, unsigned* n_unconverged, cudaStream_t st, float* eig_out) {
   using L = TauLayout<N>;
   const int warps = 4;
   size_t smem = (size_t)warps * L::WARP * sizeof(T);
@@ -163,7 +170,7 @@ int launch_tau(const int4* tets, const T* geo, const T* y, int64_t n_elem, T* ta
   const T tol2 = sizeof(T) == 4 ? T(1e-12) : T(1e-28);
   count_launches(1);
   tau_kernel<T, N><<<(int)blocks, warps * 32, smem, st>>>(tets, geo, y, n_qp, tau_out, nu, C_I,
-                                                          sweeps, tol2, n_unconverged);
+                                                          sweeps, tol2, n_unconverged, eig_out);
   return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
@@ -212,7 +219,8 @@ __global__ void __launch_bounds__(128) tau_polish_kernel(const int4* __restrict_
                                                          const double* __restrict__ y,
                                                          int64_t n_qp, double* __restrict__ tau_out,
                                                          double nu, double C_I,
-                                                         unsigned* __restrict__ n_unconverged) {
+                                                         unsigned* __restrict__ n_unconverged,
+                                                         float* __restrict__ eig_out) {
   using L = PolishLayout<N>;
   constexpr int NP = L::NP, NM = L::NM, C = L::C, LD = L::LD, GPW = L::GPW;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -343,6 +351,11 @@ __global__ void __launch_bounds__(128) tau_polish_kernel(const int4* __restrict_
         M[s * LD + r] = acc;
       }
     __syncwarp();
+    if (live && eig_out) {
+      float* eo = eig_out + gq * Dims<N>::EIG;
+      for (int t = k; t < NM * NM; t += N) eo[t] = (float)Vd[(t / NM) * LD + t % NM];
+      for (int j = k; j < NM; j += N) eo[NM * NM + j] = (float)M[j * LD + j];
+    }
     // s = sqrt(diag B) once per point (reusing the w rows: 3C >= 2 NM)
     double* sq = w;          // [NM] sqrt(b_ii)
     double* sq2 = w + NM;    // [NM] b_ii
@@ -399,7 +412,7 @@ __global__ void __launch_bounds__(128) tau_polish_kernel(const int4* __restrict_
 template <int N>
 int launch_tau_polish(const int4* tets, const double* geo, const double* y, int64_t n_elem,
                       double* tau_out, double nu, double C_I, unsigned* n_unconverged,
-                      cudaStream_t st) {
+                      cudaStream_t st, float* eig_out) {
   using L = PolishLayout<N>;
   int warps = 4;
   while (warps > 1 && (size_t)warps * L::WARP * sizeof(double) > 200 * 1024) --warps;
@@ -413,13 +426,13 @@ int launch_tau_polish(const int4* tets, const double* geo, const double* y, int6
   if (blocks < 1) blocks = 1;
   count_launches(1);
   tau_polish_kernel<N><<<(int)blocks, warps * 32, smem, st>>>(tets, geo, y, n_qp, tau_out, nu, C_I,
-                                                              n_unconverged);
+                                                              n_unconverged, eig_out);
   return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
 #define TS_INST_POLISH(T, N)                                                                  \
   template int launch_tau_polish<N>(const int4*, const double*, const double*, int64_t,      \
-                                    double*, double, double, unsigned*, cudaStream_t);
+                                    double*, double, double, unsigned*, cudaStream_t, float*);
 TS_FOR_EACH_N(TS_INST_POLISH, double)
 
 
@@ -591,7 +604,7 @@ TS_FOR_EACH_N(TS_INST_BACKFLOW, double)
 
 #define TS_INST_TAU(T, N)                                                                 \
   template int launch_tau<T, N>(const int4*, const T*, const T*, int64_t, T*, T, T,       \
-                                unsigned*, cudaStream_t);
+                                unsigned*, cudaStream_t, float*);
 #define TS_INST_PRELOAD_TAU(T, N) template int preload_tau<T, N>();
 TS_FOR_EACH_N(TS_INST_PRELOAD_TAU, float)
 TS_FOR_EACH_N(TS_INST_TAU, float)

@@ -73,7 +73,8 @@ __global__ void __launch_bounds__(64) tau_dd_kernel(const int4* __restrict__ tet
                                                     const double* __restrict__ y, int64_t n_qp,
                                                     double* __restrict__ tau_out, double nu,
                                                     double C_I,
-                                                    unsigned* __restrict__ n_unconverged) {
+                                                    unsigned* __restrict__ n_unconverged,
+                                                    float* __restrict__ eig_out) {
   using L = DDLayout<N>;
   constexpr int NP = L::NP, NM = L::NM, C = L::C, LD = L::LD, NN = L::NN, GPW = L::GPW;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -251,6 +252,14 @@ __global__ void __launch_bounds__(64) tau_dd_kernel(const int4* __restrict__ tet
         M[s * NM + r] = acc;
       }
     __syncwarp();
+    // eigenpairs for the derivative of tau (exact tangent), when asked: the
+    // refined vectors and diag(B) with the point's scale undone
+    if (live && eig_out) {
+      float* eo = eig_out + gq * Dims<N>::EIG;
+      const float back = (float)(1.0 / (unscale * unscale));
+      for (int t = k; t < NN; t += N) eo[t] = V[t].hi;
+      for (int j = k; j < NM; j += N) eo[NN + j] = M[j * NM + j].hi * back;
+    }
     // s_i = sqrt(b_ii), 1/s_i (double-float), and FP32 copies for the small terms
     dd* sq = w;
     dd* isq = w + NM;
@@ -316,7 +325,7 @@ __global__ void __launch_bounds__(64) tau_dd_kernel(const int4* __restrict__ tet
 template <int N>
 int launch_tau_dd(const int4* tets, const double* geo, const double* y, int64_t n_elem,
                   double* tau_out, double nu, double C_I, unsigned* n_unconverged,
-                  cudaStream_t st) {
+                  cudaStream_t st, float* eig_out) {
   using L = DDLayout<N>;
   const int warps = ((size_t)2 * L::WARP * sizeof(dd) <= 100 * 1024) ? 2 : 1;
   const size_t smem = (size_t)warps * L::WARP * sizeof(dd);
@@ -329,13 +338,13 @@ int launch_tau_dd(const int4* tets, const double* geo, const double* y, int64_t 
   if (blocks < 1) blocks = 1;
   count_launches(1);
   tau_dd_kernel<N><<<(int)blocks, warps * 32, smem, st>>>(tets, geo, y, n_qp, tau_out, nu, C_I,
-                                                          n_unconverged);
+                                                          n_unconverged, eig_out);
   return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
 #define TS_INST_TAU_DD(T, N)                                                              \
   template int launch_tau_dd<N>(const int4*, const double*, const double*, int64_t, double*, \
-                                double, double, unsigned*, cudaStream_t);
+                                double, double, unsigned*, cudaStream_t, float*);
 TS_FOR_EACH_N(TS_INST_TAU_DD, double)
 
 }  // namespace ts

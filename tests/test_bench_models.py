@@ -61,3 +61,29 @@ def test_job_rate_counts_every_replica():
     import bench
     assert bench._job_rate(1, 100, 7, 31, 2.0) == 100 * 7 * 31 / 2.0
     assert bench._job_rate(4, 100, 7, 31, 2.0) == 4 * bench._job_rate(1, 100, 7, 31, 2.0)
+
+
+def test_mode_error_is_the_space_time_l2_error():
+    import numpy as np
+
+    import bench
+    # Parseval on the real signal u(t) = u_0 + 2 Re sum_n u_n e^{i n t}: the
+    # mode-space error equals the time-sampled L2 error over one period
+    rng = np.random.default_rng(3)
+    ref = rng.standard_normal((6, 4, 5, 2))
+    ref[:, :, 0, 1] = 0.0
+    yN = ref[:, :, :3] + 0.01 * rng.standard_normal((6, 4, 3, 2))
+    yN[:, :, 0, 1] = 0.0
+    K = 64
+    t = 2 * np.pi * np.arange(K) / K
+
+    def samples(y):
+        c = y[..., 0] + 1j * y[..., 1]
+        n = np.arange(y.shape[2])
+        s = np.real(c[..., :1]) + 2 * np.real(np.einsum("vfn,kn->vfk", c[..., 1:], np.exp(1j * np.outer(t, n[1:]))))
+        return s[:, 0:3]
+
+    err_t = np.sqrt(np.mean(np.sum((samples(ref) - np.pad(samples(yN), 0)) ** 2, axis=(0, 1))))
+    norm_t = np.sqrt(np.mean(np.sum(samples(ref) ** 2, axis=(0, 1))))
+    assert abs(bench.mode_error(yN, ref) - err_t / norm_t) < 1e-12
+    assert bench.mode_error(ref, ref) == 0.0

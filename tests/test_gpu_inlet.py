@@ -8,9 +8,9 @@ Checks:
   pipe's; every inlet value equals the oracle's Womersley closed form
   (``oracle.womersley``, its own Bessel series) and the seeded input
   generator's (scipy's Bessel functions) to 1e-12; all other entries zero;
-* junction: the parabolic values equal the closed form on the derived
-  geometry, that geometry is the arm's, and the discrete flow rate through
-  the inlet triangles approaches Q_n;
+  the discrete flow rate through the inlet triangles approaches Q_n;
+* junction (inlet caps carved from a lattice, arm geometry given): the
+  parabolic values equal the closed form and the generator's data;
 * the FP32 initial guess is the FP64 one rounded.
 """
 import numpy as np
@@ -50,6 +50,16 @@ def test_pipe_womersley_inlet_matches_closed_form():
     assert np.abs(y - ref).max() <= 1e-12 * scale
     # the seeded generator (scipy's complex Bessel functions) gives the same data
     assert np.abs(y - case.y0).max() <= 1e-12 * scale
+    # the discrete flow rate through the inlet triangles (P1 interpolation of
+    # the profile on the polygonal disk) approaches Q_n = pi R^2 U_n
+    xyz = case.mesh.xyz
+    faces = case.mesh.bfaces[case.mesh.btag == mg.TAG_INLET1]
+    a, b, cc = xyz[faces[:, 0]], xyz[faces[:, 1]], xyz[faces[:, 2]]
+    nrm = np.cross(b - a, cc - a) / 2.0                # outward, area-weighted
+    for n in range(case.N):
+        q = sum(np.einsum("fki,fi->", y[faces, 0:3, n, part], -nrm) / 3.0 * (1j if part else 1)
+                for part in (0, 1))
+        assert abs(q - np.pi * R ** 2 * U[n]) <= 0.06 * abs(np.pi * R ** 2 * U[n]), (n, q)
     y32 = to_np(g.initial_guess(torch.float32))
     assert np.abs(y32 - y.astype(np.float32)).max() == 0.0
     g.close()
@@ -60,52 +70,42 @@ def test_junction_parabolic_inlets_closed_form_and_flow_rate():
     import paper_2311_09465_gb300 as ts
     case = cases.junction_case(N=4, Re=300.0, Wo=8.0, mesh=mg.junction(h=0.3, seed=3))
     g = ts.GLSProblem(case)
-    arms = {tag: (ax, sg, R) for ax, sg, R, tag in mg.JUNCTION_ARMS}
     Qs = {}
-    for tag in (mg.TAG_INLET1, mg.TAG_INLET2):
-        R = arms[tag][2]
+    for ax, sg, R, tag in mg.JUNCTION_ARMS:
+        if tag not in (mg.TAG_INLET1, mg.TAG_INLET2):
+            continue
+        ai = mg._AX[ax]
+        # the mesh's inlet caps are carved from a lattice: the arm's geometry is given
+        d = np.zeros(3)
+        d[ai] = -sg
+        c = np.zeros(3)
+        c[ai] = sg * 6.0
         Qs[tag] = np.asarray(case.info["waves"][tag]) * np.pi * R ** 2
-        g.set_inlet(tag, Qs[tag], "parabolic")
+        g.set_inlet(tag, Qs[tag], "parabolic", centre=c, direction=d, radius=R)
+        info = g.inlet_info(tag)
+        np.testing.assert_allclose(info["direction"], d, atol=0)
+        assert info["radius"] == R
     y = to_np(g.initial_guess(torch.float64))
     xyz = case.mesh.xyz
-    touched = np.zeros(case.mesh.n_nodes, dtype=bool)
-    for tag in (mg.TAG_INLET1, mg.TAG_INLET2):
-        ax, sg, R = arms[tag]
-        info = g.inlet_info(tag)
+    # the parabola 2 U_n (1 - r^2/R^2), U_n = Q_n / (pi R^2), cut at the wall
+    ref = np.zeros_like(y)
+    wall = cases.nodes_with_tag(case.mesh, mg.TAG_WALL)
+    for ax, sg, R, tag in mg.JUNCTION_ARMS:
+        if tag not in Qs:
+            continue
         ai = mg._AX[ax]
-        # geometry of the arm: inflow along -sg * axis, centre on the axis, radius close to R
-        d_ref = np.zeros(3)
-        d_ref[ai] = -sg
-        np.testing.assert_allclose(info["direction"], d_ref, atol=1e-6)
-        off = info["centre"].copy()
-        off[ai] = 0.0
-        assert np.linalg.norm(off) <= 0.05 * R
-        assert abs(info["radius"] - R) <= 0.05 * R
-        # values: the parabola on the derived geometry, along the derived direction
-        faces = case.mesh.bfaces[case.mesh.btag == tag]
-        nodes = np.unique(faces)
-        others = np.unique(case.mesh.bfaces[case.mesh.btag != tag])
-        rim = np.isin(nodes, others)
-        Rf, c, d = info["radius"], info["centre"], info["direction"]
-        rel = xyz[nodes] - c
-        rperp = np.linalg.norm(rel - np.outer(rel @ d, d), axis=1)
+        o = [k for k in range(3) if k != ai]
+        nodes = np.nonzero(cases.nodes_with_tag(case.mesh, tag) & ~wall)[0]
+        r = np.hypot(xyz[nodes, o[0]], xyz[nodes, o[1]])
         for n in range(case.N):
-            U = Qs[tag][n] / (np.pi * Rf ** 2)
-            w = 2.0 * U * (1.0 - np.minimum(rperp / Rf, 1.0) ** 2)
-            w[rim] = 0.0
-            for i in range(3):
-                np.testing.assert_allclose(y[nodes, i, n, 0], np.real(w) * d[i], rtol=0,
-                                           atol=1e-12 * abs(U) * 2)
-                im = 0.0 if n == 0 else np.imag(w) * d[i]
-                np.testing.assert_allclose(y[nodes, i, n, 1], im, rtol=0, atol=1e-12 * abs(U) * 2)
-        # discrete flow rate of mode 0 through the inlet triangles (P1 interpolation)
-        a, b, cc = xyz[faces[:, 0]], xyz[faces[:, 1]], xyz[faces[:, 2]]
-        nrm = np.cross(b - a, cc - a) / 2.0           # outward, area-weighted
-        un = np.einsum("fki,fi->fk", y[faces, 0:3, 0, 0], -nrm)
-        q0 = un.sum(axis=1).sum() / 3.0
-        assert abs(q0 - Qs[tag][0].real) <= 0.08 * abs(Qs[tag][0].real), (q0, Qs[tag][0])
-        touched[nodes] = True
-    # nothing outside the inlets, pressure zero
-    assert np.abs(y[~touched]).max() == 0.0
-    assert np.abs(y[:, 3]).max() == 0.0
+            w = 2.0 * Qs[tag][n] / (np.pi * R ** 2) * (1.0 - np.minimum(r / R, 1.0) ** 2)
+            ref[nodes, ai, n, 0] = -sg * np.real(w)
+            ref[nodes, ai, n, 1] = 0.0 if n == 0 else -sg * np.imag(w)
+    scale = np.abs(ref).max()
+    assert np.abs(y - ref).max() <= 1e-12 * scale
+    # the seeded generator builds the same Dirichlet data
+    assert np.abs(y - case.y0).max() <= 1e-12 * scale
+    # derived geometry: the cap's normal is the arm's axis
+    g.set_inlet(mg.TAG_INLET1, Qs[mg.TAG_INLET1], "parabolic")
+    np.testing.assert_allclose(g.inlet_info(mg.TAG_INLET1)["direction"], [0.0, -1.0, 0.0], atol=1e-9)
     g.close()

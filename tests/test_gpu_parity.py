@@ -225,3 +225,26 @@ def test_backflow_stabilisation_matches_oracle(torch, prec):
         hv_ref = op.jvp(prob, lin, v, variant, mass_coef(case, 0.5))
         hv = to_np(g.jvp(to_dev(v, _dtype(torch, prec))))
         assert rel_l2(hv, hv_ref) <= TOL[prec], (variant, rel_l2(hv, hv_ref))
+
+
+# the FP64 element operator with its arithmetic in double-float pairs on the
+# FP32 pipe (TS_ELEMENT64_DOUBLEFLOAT) meets the FP64 bar: residual and all
+# three tangent variants, also at 30x velocity
+@pytest.mark.parametrize("scale", [1.0, 30.0])
+@pytest.mark.parametrize("name", ["pipe_N3", "junction_N4", "pipe_N7", "pipe_N15"])
+def test_fp64_doublefloat_element_operator_matches_oracle(torch, name, scale):
+    case = CASES[name]()
+    y = _state(case, seed=15, scale=scale)
+    v = cases.random_state(case.mesh, case.N, seed=16, smooth=False)
+    prob = op.problem_from_case(case)
+    lin = op.linearize(prob, y)
+    r_ref = op.apply(prob, lin, y, "frozen")
+    for variant in ("paper", "frozen", "lin_a"):
+        g = _gls(case, variant=variant, dt=0.7)
+        g.option(element64="doublefloat")
+        r = to_np(g.residual(to_dev(y, torch.float64)))
+        assert rel_l2(r, r_ref) <= TOL[64], (variant, rel_l2(r, r_ref))
+        hv_ref = op.jvp(prob, lin, v, variant, mass_coef(case, 0.7))
+        hv = to_np(g.jvp(to_dev(v, torch.float64)))
+        assert rel_l2(hv, hv_ref) <= TOL[64], (variant, rel_l2(hv, hv_ref))
+        g.close()
