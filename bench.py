@@ -454,14 +454,46 @@ def _time_to_residual(ts, torch, case, g, args):
     out["pipe"] = res
     out["batched"] = _batched_ttr(ts, torch)
     out["surrogate"] = _surrogate_ttr(ts, torch)
-    if args.solve_steps > 0:
-        # the bench junction, mixed precision, capped: at Re 500 this solve does not
-        # reach 1e-8 (its residual history is reported as measured)
-        g.set(dt_pseudo=args.dt, variant="lin_a")
-        _, rep = _one_solve(ts, torch, g, case.y0, 32, args.solve_steps)
-        rep["workload"] = f"junction, {case.mesh.n_tets} tets, N=7, Re 500, Wo 10"
-        out["junction_mixed"] = rep
+    out["junction"] = _junction_ttr(ts, torch, case, args)
     return out
+
+
+JUNCTION_SOLVE = dict(tol=1e-8, max_steps=120, krylov=100, eps_ls=0.05, max_matvec=1000, precond=3, ser=1.0,
+                      dt_max=2.0, reject=4.0, raise_on_noconv=False)
+
+
+def _junction_ttr(ts, torch, case, args):
+    """Time to ||r|| <= 1e-8 r_ref on the bench junction (188k tets, N = 7, Wo 10,
+    resistance outlets) at the largest Re this solver converges from the paper's
+    initial guess, Re 100: mixed precision (FP32 LIN_A products, FP64 GMRES and
+    outer residual) always; plain FP64 (FP64 products and tau refinement) with
+    --junction-fp64 (about 15 minutes on one GB300).  The inflow is set through
+    ts_set_inlet; r_ref is the norm at the initial guess."""
+    from workloads import cases
+    jc = cases.junction_case(N=case.N, Re=args.junction_re, Wo=10.0, wave_seed=100, resistance=1.0,
+                             mesh=case.mesh, amp=WAVE_AMP)
+    res = {"workload": f"junction {jc.mesh.n_tets} tets, N={jc.N}, Re {args.junction_re}, Wo 10, resistance R=1",
+           "solver": {k: v for k, v in JUNCTION_SOLVE.items() if k != "raise_on_noconv"}}
+    legs = [("mixed", 32, "doublefloat")] + ([("fp64", 64, "refine")] if args.junction_fp64 else [])
+    fields = {}
+    for name, prec, tau64 in legs:
+        g = ts.GLSProblem(jc, variant="lin_a", dt_pseudo=0.2, tau64=tau64)
+        y = _library_inflow(g, jc)
+        r_ref = float(g.residual(y).norm())
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rep = g.solve(y, precision=prec, r_ref=r_ref, **JUNCTION_SOLVE)
+        torch.cuda.synchronize()
+        res[name] = {"seconds": time.perf_counter() - t0, "converged": rep["status"] == 0, "r_final": rep["r_final"],
+                     "steps": rep["steps"], "matvecs": rep["matvecs"], "t_residual": rep["t_residual"],
+                     "t_jvp": rep["t_jvp"], "t_krylov": rep["t_krylov"], "t_precond": rep["t_precond"],
+                     "tau64": tau64}
+        fields[name] = y
+        g.close()
+    if "fp64" in fields and res["mixed"]["converged"] and res["fp64"]["converged"]:
+        res["speedup_mixed_over_fp64"] = res["fp64"]["seconds"] / res["mixed"]["seconds"]
+        res["field_rel_l2_mixed_vs_fp64"] = float((fields["mixed"] - fields["fp64"]).norm() / fields["fp64"].norm())
+    return res
 
 
 def _pipe_family(rng, n, meshes):
@@ -774,6 +806,60 @@ def run_mode_study(args, Ns=(2, 3, 5, 7, 10), N_ref=15, h=0.3, Re=100.0, Wo=10.0
     return out
 
 
+def run_assembled(args, R=20):
+    """The assembled block-structured tangent of the paper's variant (section
+    2.5.2) on the bench junction: assembly time, storage, and the SpMV against
+    the matrix-free product of the same variant (CUDA events, one JSON line).
+    HBM roofline of the SpMV: the records, their column ids and row offsets,
+    x and Hv once each, against the measured copy bandwidth."""
+    import torch
+
+    import paper_2311_09465_gb300 as ts
+
+    case = _workload()
+    g = ts.GLSProblem(case, variant="paper", dt_pseudo=args.dt)
+    y = _library_inflow(g, case)
+    g.residual(y)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    g.assemble()
+    ev[0].record()
+    g.assemble()
+    ev[1].record()
+    torch.cuda.synchronize()
+    t_asm = ev[0].elapsed_time(ev[1]) / 1e3
+    v = torch.tensor(np.random.default_rng(0).standard_normal(y.shape), dtype=torch.float32, device="cuda")
+    hv, hm = torch.empty_like(v), torch.empty_like(v)
+    for _ in range(3):
+        g.spmv(v, hv)
+        g.jvp(v, hm)
+    ev[0].record()
+    for _ in range(R):
+        g.spmv(v, hv)
+    ev[1].record()
+    torch.cuda.synchronize()
+    t_spmv = ev[0].elapsed_time(ev[1]) / 1e3 / R
+    ev[0].record()
+    for _ in range(R):
+        g.jvp(v, hm)
+    ev[1].record()
+    torch.cuda.synchronize()
+    t_mf = ev[0].elapsed_time(ev[1]) / 1e3 / R
+    nnz = ts.ts_mesh_connections(g.mesh)
+    rec = g.assembled_bytes()
+    V, N, E = case.mesh.n_nodes, case.N, case.mesh.n_tets
+    alg = rec + 4 * nnz + 4 * (V + 1) + 2 * V * 8 * N * 4
+    peak, peak_kind = _peaks()
+    out = {"assembled": "paper-variant tangent, block-structured (section 2.5.2)",
+           "workload": f"junction {E} tets, N={N}", "connections": nnz, "record_bytes": rec,
+           "assembly_ms": t_asm * 1e3, "spmv_ms": t_spmv * 1e3, "matrix_free_paper_ms": t_mf * 1e3,
+           "spmv_element_mode_evals_per_s": E * N / t_spmv,
+           "rel_l2_spmv_vs_matrix_free": float((hv - hm).norm() / hm.norm()),
+           "roofline": {"bound": "hbm", "achieved": alg / t_spmv / 1e9, "peak": peak, "unit": "GB/s",
+                        "frac": alg / t_spmv / 1e9 / peak, "algorithmic_bytes": alg, "peak_source": peak_kind}}
+    print(json.dumps(out), flush=True)
+    g.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -782,17 +868,23 @@ def main():
     ap.add_argument("--impl", default="gls", choices=["gls", "reference"])
     ap.add_argument("--dt", type=float, default=0.2, help="pseudo-time step")
     ap.add_argument("--no-solve", dest="solve", action="store_false")
-    ap.add_argument("--solve-steps", type=int, default=0,
-                    help="also run the junction mixed solve for this many steps")
+    ap.add_argument("--junction-re", type=float, default=100.0,
+                    help="Reynolds number of the junction time-to-1e-8 solve")
+    ap.add_argument("--junction-fp64", action="store_true",
+                    help="also time the plain FP64 junction solve (about 15 minutes)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=400)
     ap.add_argument("--ref-sample", type=int, default=200)
+    ap.add_argument("--assembled", action="store_true",
+                    help="assembled paper-variant tangent and its SpMV on the junction (its own JSON line)")
     ap.add_argument("--mode-study", action="store_true",
                     help="solution error vs number of modes against a 15-mode reference (its own JSON line)")
     ap.add_argument("--sweep", action="store_true",
                     help="mode sweep N = 3, 7, 15 on the junction (its own JSON line) instead of the bench")
     args = ap.parse_args()
-    if args.mode_study:
+    if args.assembled:
+        run_assembled(args)
+    elif args.mode_study:
         run_mode_study(args)
     elif args.sweep:
         run_sweep(args)
