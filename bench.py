@@ -332,13 +332,16 @@ def run_gpu(args):
     t_res64_all = e0.elapsed_time(e1) / 1e3 / 3
     v64 = v32.double()
     hv64 = torch.empty_like(v64)
-    ts.ts_jvp(g.prob, v64, hv64)
-    e0.record(stream)
-    for _ in range(5):
+    t_jvp64 = {}
+    for elem in ("native", "doublefloat"):
+        g.option(element64=elem)
         ts.ts_jvp(g.prob, v64, hv64)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t_jvp64 = e0.elapsed_time(e1) / 1e3 / 5
+        e0.record(stream)
+        for _ in range(5):
+            ts.ts_jvp(g.prob, v64, hv64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_jvp64[elem] = e0.elapsed_time(e1) / 1e3 / 5
     peak, peak_kind = _peaks()
     alg = _jvp_bytes_model(case)
     alg_lin_a = _jvp_bytes(case)
@@ -401,9 +404,11 @@ def run_gpu(args):
         "operator_throughput": {
             "unit": "element-mode evals/s",
             "residual_fp64": E * N / t_res64_all, "residual_fp32": E * N / t_res32,
-            "jvp_fp32": E * N / t_jvp, "jvp_fp64": E * N / t_jvp64,
+            "jvp_fp32": E * N / t_jvp, "jvp_fp64": E * N / t_jvp64["native"],
+            "jvp_fp64_doublefloat": E * N / t_jvp64["doublefloat"],
             "ms": {"residual_fp64": t_res64_all * 1e3, "residual_fp32": t_res32 * 1e3,
-                   "jvp_fp32": t_jvp * 1e3, "jvp_fp64": t_jvp64 * 1e3}},
+                   "jvp_fp32": t_jvp * 1e3, "jvp_fp64": t_jvp64["native"] * 1e3,
+                   "jvp_fp64_doublefloat": t_jvp64["doublefloat"] * 1e3}},
         "cpu_baseline": cpu,
         "clocks": clk,
         "breakdown": {"jvp_fp32_ms": t_jvp * 1e3, "jvp_element_kernel_ms": t_jel * 1e3,
@@ -417,6 +422,13 @@ def run_gpu(args):
     g.close()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def _elem64(tau64):
+    """The plain FP64 legs run every FP64 operation as FP64 instructions
+    (tau by the FP64 refinement, the native FP64 element operator); the mixed
+    legs use the library defaults (double-float tau and element pass)."""
+    return "native" if tau64 == "refine" else None
 
 
 def _one_solve(ts, torch, g, y0, prec, max_steps):
@@ -440,7 +452,7 @@ def _time_to_residual(ts, torch, case, g, args):
     # mixed: FP32 tangent products, FP64 GMRES, outer residual with double-float tau;
     # plain FP64: FP64 products and the FP64 tau refinement
     for prec, tau64 in ((32, "doublefloat"), (64, "refine")):
-        gp = ts.GLSProblem(pipe, variant="lin_a", dt_pseudo=0.5, tau64=tau64)
+        gp = ts.GLSProblem(pipe, variant="lin_a", dt_pseudo=0.5, tau64=tau64, element64=_elem64(tau64))
         yy, rep = _one_solve(ts, torch, gp, pipe.y0, prec, 60)
         rep["tau64"] = tau64
         res["mixed" if prec == 32 else "fp64"] = rep
@@ -477,7 +489,7 @@ def _junction_ttr(ts, torch, case, args):
     legs = [("mixed", 32, "doublefloat")] + ([("fp64", 64, "refine")] if args.junction_fp64 else [])
     fields = {}
     for name, prec, tau64 in legs:
-        g = ts.GLSProblem(jc, variant="lin_a", dt_pseudo=0.2, tau64=tau64)
+        g = ts.GLSProblem(jc, variant="lin_a", dt_pseudo=0.2, tau64=tau64, element64=_elem64(tau64))
         y = _library_inflow(g, jc)
         r_ref = float(g.residual(y).norm())
         torch.cuda.synchronize()
@@ -521,7 +533,7 @@ def _batched_ttr(ts, torch):
     for prec, tau64 in ((32, "doublefloat"), (64, "refine")):
         t, ok, fields = 0.0, True, []
         for c, _, _ in inst:
-            g = ts.GLSProblem(c, variant="lin_a", dt_pseudo=0.5, tau64=tau64)
+            g = ts.GLSProblem(c, variant="lin_a", dt_pseudo=0.5, tau64=tau64, element64=_elem64(tau64))
             y = torch.tensor(c.y0, dtype=torch.float64, device="cuda")
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -589,7 +601,7 @@ def _surrogate_ttr(ts, torch, n_train=32, n_test=4):
         row = {}
         for name, prec, tau64, guess in (("fp64_plain", 64, "refine", False), ("mixed_plain", 32, "doublefloat", False),
                                           ("mixed_surrogate", 32, "doublefloat", True)):
-            g = ts.GLSProblem(c, variant="lin_a", dt_pseudo=0.5, tau64=tau64)
+            g = ts.GLSProblem(c, variant="lin_a", dt_pseudo=0.5, tau64=tau64, element64=_elem64(tau64))
             y = torch.tensor(c.y0, dtype=torch.float64, device="cuda")
             r_ref = float(g.residual(y).norm())
             torch.cuda.synchronize()
@@ -611,6 +623,90 @@ def _surrogate_ttr(ts, torch, n_train=32, n_test=4):
             "held_out": agg,
             "speedup_surrogate_over_fp64_plain": agg["fp64_plain"]["seconds"] / agg["mixed_surrogate"]["seconds"],
             "speedup_surrogate_over_mixed_plain": agg["mixed_plain"]["seconds"] / agg["mixed_surrogate"]["seconds"]}
+
+
+def run_surrogate_junction(args, n_train=130, n_test=8, h=0.4, N=7, hidden=512, n_out=128):
+    """The learned initial guess at the junction configuration's shape: inputs
+    the 16 inflow coefficients (2 inlets x harmonics 1..4 x Re/Im) plus Re and
+    Wo, 3 hidden tanh layers of 512, 128 POD coefficients; trained by the
+    library's kernels on junction solves of the method (Re ~ U(60, 140), the
+    range this solver converges from the plain guess, Wo 10, own 1/n^2 inflow
+    per inlet); held-out solves to 1e-8 r_ref from the plain and the learned
+    guess (one JSON line).  The training fields are converged to 1e-6 r_ref."""
+    import torch
+
+    import paper_2311_09465_gb300 as ts
+    from workloads import cases, meshgen as mg
+
+    mesh = mg.junction(h=h, seed=1)
+    rng = np.random.default_rng(5000)
+    opts = dict(tol=1e-8, max_steps=100, krylov=100, eps_ls=0.05, max_matvec=1000, precond=3, ser=1.0,
+                dt_max=2.0, raise_on_noconv=False)
+
+    def sample():
+        Re = float(rng.uniform(60.0, 140.0))
+        seed = int(rng.integers(0, 2 ** 31))
+        c = cases.junction_case(N=N, Re=Re, Wo=10.0, wave_seed=seed, resistance=1.0, mesh=mesh, amp=0.2)
+        x = cases.surrogate_inputs([c.info["waves"][mg.TAG_INLET1], c.info["waves"][mg.TAG_INLET2]], Re, 10.0)
+        return c, x, Re
+
+    X, Y = [], []
+    t0 = time.perf_counter()
+    n_conv = 0
+    for _ in range(n_train):
+        c, x, Re = sample()
+        g = ts.GLSProblem(c, variant="lin_a", dt_pseudo=0.2)
+        y = _library_inflow(g, c)
+        rep = g.solve(y, precision=32, **dict(opts, tol=1e-6))   # training data: 1e-6 r_ref
+        n_conv += rep["status"] == 0
+        X.append(x)
+        Y.append(y.reshape(-1))
+        g.close()
+    t_solves = time.perf_counter() - t0
+    Yd = torch.stack(Y)
+    sur = ts.Surrogate(len(X[0]), hidden, 3, n_out, Yd.shape[1], seed=7)
+    sigma = sur.fit_basis(Yd)
+    hist = sur.train(np.array(X), Yd, epochs=4000, batch=32, lr=1e-3, seed=8)
+    t_train = time.perf_counter() - t0 - t_solves
+    rows = []
+    for _ in range(n_test):
+        c, x, Re = sample()
+        row = {}
+        for name, guess in (("plain", False), ("learned", True)):
+            g = ts.GLSProblem(c, variant="lin_a", dt_pseudo=0.2)
+            y = _library_inflow(g, c)
+            r_ref = float(g.residual(y).norm())
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            if guess:
+                sur.guess(g, x, y)
+            r0 = float(g.residual(y).norm()) / r_ref
+            rep = g.solve(y, precision=32, r_ref=r_ref, **opts)
+            torch.cuda.synchronize()
+            row[name] = {"seconds": time.perf_counter() - t1, "steps": rep["steps"], "matvecs": rep["matvecs"],
+                         "converged": rep["status"] == 0, "r0_over_r_ref": r0}
+            if guess:
+                row["field"] = y
+            else:
+                y_plain = y
+            g.close()
+        row["field_rel_l2_learned_vs_plain"] = float((row.pop("field") - y_plain).norm() / y_plain.norm())
+        rows.append(row)
+    sur.close()
+    agg = {k: {"seconds": sum(r[k]["seconds"] for r in rows), "steps": sum(r[k]["steps"] for r in rows),
+               "matvecs": sum(r[k]["matvecs"] for r in rows),
+               "converged": all(r[k]["converged"] for r in rows)} for k in ("plain", "learned")}
+    out = {"surrogate": "junction", "workload": f"junction {mesh.n_tets} tets, N={N}, Re U(60,140), Wo 10, "
+                                                 f"1/n^2 inflow x 0.2 per inlet",
+           "network": f"{len(X[0])}-{hidden}x3-{n_out} tanh", "train_solves": n_train,
+           "train_solves_converged": int(n_conv), "pod_rank": int(len(sigma)), "held_out": n_test,
+           "solve_seconds": t_solves, "train_seconds": t_train,
+           "train_loss_first_last": [float(hist[0]), float(hist[-1])], "held_out_totals": agg,
+           "speedup_learned_over_plain": agg["plain"]["seconds"] / agg["learned"]["seconds"],
+           "max_field_rel_l2_learned_vs_plain": max(r["field_rel_l2_learned_vs_plain"] for r in rows),
+           "mean_r0_over_r_ref_learned": float(np.mean([r["learned"]["r0_over_r_ref"] for r in rows]))}
+    print(json.dumps(out), flush=True)
+    return out
 
 
 def _oracle_step_rate(case, n_elem, n_jvp, seed=0):
@@ -860,6 +956,16 @@ def run_assembled(args, R=20):
     g.close()
 
 
+def run_junction_ttr(args):
+    """Only the junction time-to-1e-8 leg (its own JSON line)."""
+    import torch
+
+    import paper_2311_09465_gb300 as ts
+    case = _workload()
+    out = _junction_ttr(ts, torch, case, args)
+    print(json.dumps({"time_to_residual_1e-8": {"junction": out}}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -875,6 +981,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=400)
     ap.add_argument("--ref-sample", type=int, default=200)
+    ap.add_argument("--junction-ttr", action="store_true",
+                    help="only the junction time-to-1e-8 leg (its own JSON line; with --junction-fp64 both legs)")
+    ap.add_argument("--surrogate-junction", action="store_true",
+                    help="learned initial guess at the junction configuration's network shape (its own JSON line)")
     ap.add_argument("--assembled", action="store_true",
                     help="assembled paper-variant tangent and its SpMV on the junction (its own JSON line)")
     ap.add_argument("--mode-study", action="store_true",
@@ -882,7 +992,11 @@ def main():
     ap.add_argument("--sweep", action="store_true",
                     help="mode sweep N = 3, 7, 15 on the junction (its own JSON line) instead of the bench")
     args = ap.parse_args()
-    if args.assembled:
+    if args.junction_ttr:
+        run_junction_ttr(args)
+    elif args.surrogate_junction:
+        run_surrogate_junction(args)
+    elif args.assembled:
         run_assembled(args)
     elif args.mode_study:
         run_mode_study(args)

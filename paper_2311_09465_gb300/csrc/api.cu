@@ -144,7 +144,7 @@ struct ts_problem {
   bool sev_res = false, sev_jvp = false;
   bool fast32 = true;    // FP32 products with the single-launch kernel (jvp32.cu)
   int tau64 = TS_TAU64_DOUBLEFLOAT;  // how the FP64 residual computes tau
-  int elem64 = TS_ELEMENT64_NATIVE;  // arithmetic of the FP64 element operator
+  int elem64 = TS_ELEMENT64_DOUBLEFLOAT;  // arithmetic of the FP64 element operator
 };
 
 // ------------------------------------------------------------------ helpers

@@ -217,8 +217,19 @@ __global__ void __launch_bounds__(128)
   }
 }
 
+// 16-byte asynchronous global -> shared copies (LDGSTS), grouped per stage
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory"); }
+
 // y = H x on the assembled records; Dirichlet velocity and Im(mode 0) inputs
-// are ignored and the same rows of y are zero
+// are ignored and the same rows of y are zero.  The record and x_B of the
+// next connection are copied into shared memory (double buffer) while the
+// current one is multiplied, so a warp keeps one record in flight.
 template <int N>
 __global__ void __launch_bounds__(256)
     spmv_paper_kernel(const int32_t* __restrict__ row_off, const int32_t* __restrict__ cols,
@@ -230,22 +241,34 @@ __global__ void __launch_bounds__(256)
   extern __shared__ __align__(16) float smem_f[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
-  float* rec = smem_f + warp * L::PWARP;
-  float* xs = rec + HB;
+  float* buf0 = smem_f + warp * 2 * L::PWARP;   // [2][HB + NB]
+  auto stage = [&](int p, float* dst) {
+    const float4* src = reinterpret_cast<const float4*>(H + (int64_t)p * HB);
+    for (int t = lane; t < HB / 4; t += 32) cp_async16(dst + 4 * t, src + t);
+    const float4* xb = reinterpret_cast<const float4*>(x + (int64_t)cols[p] * NB);
+    for (int t = lane; t < NB / 4; t += 32) cp_async16(dst + HB + 4 * t, xb + t);
+    cp_async_commit();
+  };
   for (int64_t A = (int64_t)blockIdx.x * wpb + warp; A < n_nodes; A += (int64_t)gridDim.x * wpb) {
     float acc[R];
 #pragma unroll
     for (int k = 0; k < R; ++k) acc[k] = 0.f;
     const int r0 = row_off[A], r1 = row_off[A + 1];
+    if (r0 < r1) stage(r0, buf0);
     for (int p = r0; p < r1; ++p) {
-      const int B = cols[p];
-      const float4* src = reinterpret_cast<const float4*>(H + (int64_t)p * HB);
-      for (int t = lane; t < HB / 4; t += 32) reinterpret_cast<float4*>(rec)[t] = __ldg(src + t);
-      const bool dirB = dmask[B] != 0;
+      float* rec = buf0 + ((p - r0) & 1) * L::PWARP;
+      float* xs = rec + HB;
+      if (p + 1 < r1) {
+        stage(p + 1, buf0 + ((p + 1 - r0) & 1) * L::PWARP);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncwarp();
+      const bool dirB = dmask[cols[p]] != 0;
       for (int t = lane; t < NB; t += 32) {
         const int f = t / C, c = t - f * C;
-        const float v = x[(int64_t)B * NB + t];
-        xs[t] = (c == 1 || (dirB && f < 3)) ? 0.f : v;
+        if (c == 1 || (dirB && f < 3)) xs[t] = 0.f;
       }
       __syncwarp();
 #pragma unroll
@@ -254,17 +277,24 @@ __global__ void __launch_bounds__(256)
         if (o < NB) {
           const int f = o / C, r = o - f * C;
           float s = acc[k];
+          // rows and x slices start at multiples of 2 floats: 8-byte shared loads
           if (f < 3) {
-            const float* Kr = rec + r * C;
-            const float* xi = xs + f * C;
+            const float2* Kr = reinterpret_cast<const float2*>(rec + r * C);
+            const float2* xi = reinterpret_cast<const float2*>(xs + f * C);
 #pragma unroll
-            for (int c = 0; c < C; ++c) s = fmaf(Kr[c], xi[c], s);
+            for (int c = 0; c < C / 2; ++c) {
+              const float2 a = Kr[c], b = xi[c];
+              s = fmaf(a.x, b.x, fmaf(a.y, b.y, s));
+            }
             s = fmaf(rec[2 * CC + f], xs[3 * C + r], s);
           } else {
-            const float* Lr = rec + CC + r * C;
-            const float* xp = xs + 3 * C;
+            const float2* Lr = reinterpret_cast<const float2*>(rec + CC + r * C);
+            const float2* xp = reinterpret_cast<const float2*>(xs + 3 * C);
 #pragma unroll
-            for (int c = 0; c < C; ++c) s = fmaf(Lr[c], xp[c], s);
+            for (int c = 0; c < C / 2; ++c) {
+              const float2 a = Lr[c], b = xp[c];
+              s = fmaf(a.x, b.x, fmaf(a.y, b.y, s));
+            }
             s = fmaf(rec[2 * CC + 3], xs[r], s);
             s = fmaf(rec[2 * CC + 4], xs[C + r], s);
             s = fmaf(rec[2 * CC + 5], xs[2 * C + r], s);
@@ -422,7 +452,7 @@ int launch_spmv_paper(const int32_t* row_off, const int32_t* cols, const float* 
   using L = AsmLayout<N>;
   if (n_nodes <= 0) return 0;
   const int warps = 8;
-  const size_t smem = (size_t)warps * L::PWARP * sizeof(float);
+  const size_t smem = (size_t)warps * 2 * L::PWARP * sizeof(float);
   if (smem > 227 * 1024) return -6;
   cudaFuncSetAttribute(spmv_paper_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int64_t blocks = (n_nodes + warps - 1) / warps;
