@@ -419,6 +419,18 @@ int  ts_tracer_set_dirichlet(ts_tracer* tracer, int tag);
 int  ts_tracer_residual(ts_tracer* tracer, const void* a, const void* phi, void* r, int precision,
                         void* stream);
 
+/* 1 (default): the GLS residual above; 0: its Galerkin terms only (tau = 0),
+ * the unstabilised method the paper compares against (section 3.3). */
+int  ts_tracer_set_stabilised(ts_tracer* tracer, int gls);
+/* Solves r(phi) = 0 for phi_inout (FP64 device [V][N][2]; the Dirichlet values
+ * already in place, the other entries the start) on the advecting velocity a
+ * (FP64 device [V][3][N][2]): restarted GMRES(krylov <= 128) with two-pass
+ * classical Gram-Schmidt in FP64 on the linear operator, to ||r|| <= tol
+ * ||r(phi_in)||.  *matvecs_out, *rel_out: operator applications and final
+ * relative residual.  TS_ERR_NOCONV at max_matvec. */
+int  ts_tracer_solve(ts_tracer* tracer, const double* a, double* phi_inout, double tol, int krylov,
+                     int max_matvec, int* matvecs_out, double* rel_out, void* stream);
+
 /* Thread-local message describing the last error. */
 const char* ts_last_error(void);
 

@@ -132,6 +132,9 @@ def lib() -> ctypes.CDLL:
     L.ts_tracer_free.restype = None
     L.ts_tracer_set_dirichlet.argtypes = [vp, ctypes.c_int]
     L.ts_tracer_residual.argtypes = [vp, vp, vp, vp, ctypes.c_int, vp]
+    L.ts_tracer_set_stabilised.argtypes = [vp, ctypes.c_int]
+    L.ts_tracer_solve.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                  ctypes.POINTER(ctypes.c_int), dp, vp]
     L.ts_last_error.restype = ctypes.c_char_p
     L.ts_version.restype = ctypes.c_char_p
     L.ts_launch_count.restype = ctypes.c_int64
@@ -699,6 +702,22 @@ def ts_tracer_residual(tracer, a, phi, r, stream=None):
     return r
 
 
+def ts_tracer_set_stabilised(tracer, gls):
+    _check(lib().ts_tracer_set_stabilised(tracer, int(gls)))
+
+
+def ts_tracer_solve(tracer, a, phi, tol=1e-10, krylov=100, max_matvec=20000, stream=None):
+    """phi (FP64 CUDA [V, N, 2], Dirichlet values in place) <- root of the tracer residual."""
+    import torch
+    for t in (a, phi):
+        if not t.is_cuda or not t.is_contiguous() or t.dtype != torch.float64:
+            raise ValueError("a and phi must be contiguous CUDA float64 tensors")
+    nmv, rel = ctypes.c_int(), ctypes.c_double()
+    _check(lib().ts_tracer_solve(tracer, ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(phi.data_ptr()), tol,
+                                 krylov, max_matvec, ctypes.byref(nmv), ctypes.byref(rel), _stream_ptr(stream)))
+    return {"matvecs": nmv.value, "rel": rel.value}
+
+
 class Tracer:
     """Time-spectral GLS convection-diffusion residual of a scalar on a mesh
     (ts_tracer_*); phi and r are CUDA tensors [V, N, 2], the velocity a [V, 3, N, 2]."""
@@ -712,6 +731,12 @@ class Tracer:
     def residual(self, a, phi, r=None, stream=None):
         import torch
         return ts_tracer_residual(self.h, a, phi, torch.empty_like(phi) if r is None else r, stream)
+
+    def stabilised(self, gls=True):
+        ts_tracer_set_stabilised(self.h, gls)
+
+    def solve(self, a, phi, tol=1e-10, krylov=100, max_matvec=20000, stream=None):
+        return ts_tracer_solve(self.h, a, phi, tol, krylov, max_matvec, stream)
 
     def close(self):
         if getattr(self, "h", None):

@@ -1442,6 +1442,10 @@ struct ts_tracer {
   double *a4_64 = nullptr, *tau64 = nullptr, *dft64 = nullptr;
   float *a4_32 = nullptr, *tau32 = nullptr, *dft32 = nullptr;
   unsigned* d_counter = nullptr;
+  int gls = 1;                       // 0: Galerkin terms only (no least-squares term)
+  // solve workspace (FP64)
+  double *basis = nullptr, *w = nullptr, *r = nullptr, *dphi = nullptr, *partial = nullptr, *h = nullptr;
+  int basis_m = 0;
 };
 
 namespace {
@@ -1465,8 +1469,9 @@ double*& tr_dft<double>(ts_tracer* t) { return t->dft64; }
 template <>
 float*& tr_dft<float>(ts_tracer* t) { return t->dft32; }
 
+// advecting velocity and tau of the tracer (once per velocity)
 template <typename T, int N>
-int tracer_residual_impl(ts_tracer* tr, const T* a, const T* phi, T* r, cudaStream_t st) {
+int tracer_prepare(ts_tracer* tr, const T* a, cudaStream_t st) {
   const ts_mesh* m = tr->mesh;
   T*& a4 = tr_a4<T>(tr);
   T*& tau = tr_tau<T>(tr);
@@ -1492,11 +1497,129 @@ int tracer_residual_impl(ts_tracer* tr, const T* a, const T* phi, T* r, cudaStre
     rc = launch_tau<float, N>(m->d_tets, m->d_geo32, a4, m->E, tau, (float)tr->kappa, (float)tr->C_I,
                               tr->d_counter, st);
   if (rc) return fail(TS_ERR_CUDA, "tau kernel launch failed");
+  return 0;
+}
+
+// r = r(phi) with the prepared velocity and tau
+template <typename T, int N>
+int tracer_apply(ts_tracer* tr, const T* phi, T* r, cudaStream_t st) {
+  const ts_mesh* m = tr->mesh;
   TS_CUDA(cudaMemsetAsync(r, 0, (size_t)m->V * tr->C * sizeof(T), st));
   for (size_t c = 0; c + 1 < m->colour_off.size(); ++c)
-    if (launch_tracer<T, N>(m->d_tets, geo_of<T>(m), a4, phi, tau, tr->d_dmask, r, dft, tr->kappa, tr->omega,
-                            m->colour_off[c], m->colour_off[c + 1], st))
+    if (launch_tracer<T, N>(m->d_tets, geo_of<T>(m), tr_a4<T>(tr), phi, tr_tau<T>(tr), tr->d_dmask, r,
+                            tr_dft<T>(tr), tr->kappa, tr->omega, m->colour_off[c], m->colour_off[c + 1], st,
+                            tr->gls))
       return fail(TS_ERR_CUDA, "tracer kernel launch failed");
+  return 0;
+}
+
+template <typename T, int N>
+int tracer_residual_impl(ts_tracer* tr, const T* a, const T* phi, T* r, cudaStream_t st) {
+  TS_TRY(tracer_prepare<T, N>(tr, a, st));
+  return tracer_apply<T, N>(tr, phi, r, st);
+}
+
+double tracer_dnorm(ts_tracer* tr, const double* x, int64_t n, cudaStream_t st, int* rc) {
+  *rc = krylov_dots(x, n, 1, x, n, tr->partial, tr->h + 300, st);
+  double h = 0;
+  if (!*rc) *rc = cudaMemcpyAsync(&h, tr->h + 300, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess;
+  if (!*rc) *rc = cudaStreamSynchronize(st) != cudaSuccess;
+  return std::sqrt(std::max(h, 0.0));
+}
+
+// restarted GMRES (classical Gram-Schmidt, two passes) on the linear tracer
+// operator: phi += d with r(phi) + A d = 0, d zero on the Dirichlet nodes
+template <int N>
+int tracer_solve_impl(ts_tracer* tr, const double* a, double* phi, double tol, int m, int max_matvec,
+                      int* matvecs, double* rel, cudaStream_t st) {
+  const int64_t n = tr->mesh->V * (int64_t)tr->C;
+  if (tr->basis_m < m + 1) {
+    dfree(tr->basis);
+    TS_TRY(dalloc(&tr->basis, (size_t)(m + 1) * n));
+    tr->basis_m = m + 1;
+  }
+  if (!tr->w) {
+    TS_TRY(dalloc(&tr->w, n));
+    TS_TRY(dalloc(&tr->r, n));
+    TS_TRY(dalloc(&tr->dphi, n));
+    TS_TRY(dalloc(&tr->partial, (size_t)krylov_partial_blocks() * 130));
+    TS_TRY(dalloc(&tr->h, 512));
+  }
+  TS_TRY(tracer_prepare<double, N>(tr, a, st));
+  TS_TRY(tracer_apply<double, N>(tr, phi, tr->r, st));
+  int rc = 0;
+  const double bnorm = tracer_dnorm(tr, tr->r, n, st, &rc);
+  if (rc) return fail(TS_ERR_CUDA, "tracer solve: norm");
+  *matvecs = 0;
+  *rel = 1.0;
+  if (bnorm == 0) return 0;
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), yk(m);
+  TS_CUDA(cudaMemsetAsync(tr->dphi, 0, n * sizeof(double), st));
+  // the current linear residual b - A d (b = -r(phi0)) is -w
+  TS_CUDA(cudaMemcpyAsync(tr->w, tr->r, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  double beta = bnorm;
+  int nmv = 0;
+  while (true) {
+    if (vec_scale(tr->basis, tr->w, -1.0 / beta, n, st)) return fail(TS_ERR_CUDA, "scale");
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int k_used = 0;
+    for (int k = 0; k < m; ++k) {
+      TS_TRY(tracer_apply<double, N>(tr, tr->basis + (int64_t)k * n, tr->w, st));
+      ++nmv;
+      double* h1 = tr->h;
+      double* h2 = tr->h + 130;
+      if (krylov_dots(tr->basis, n, k + 1, tr->w, n, tr->partial, h1, st) ||
+          krylov_sub(tr->w, tr->basis, n, k + 1, h1, n, st) ||
+          krylov_dots(tr->basis, n, k + 1, tr->w, n, tr->partial, h2, st) ||
+          krylov_sub(tr->w, tr->basis, n, k + 1, h2, n, st) ||
+          krylov_dots(tr->w, n, 1, tr->w, n, tr->partial, tr->h + 260, st) ||
+          vec_normalise(tr->basis + (int64_t)(k + 1) * n, tr->w, tr->h + 260, n, st))
+        return fail(TS_ERR_CUDA, "tracer solve: Gram-Schmidt");
+      double hh[391];
+      TS_CUDA(cudaMemcpyAsync(hh, tr->h, 261 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      TS_CUDA(cudaStreamSynchronize(st));
+      double hcol[130];
+      for (int j = 0; j <= k; ++j) hcol[j] = hh[j] + hh[130 + j];
+      const double hn = std::sqrt(std::max(hh[260], 0.0));
+      hcol[k + 1] = hn;
+      for (int j = 0; j < k; ++j) {
+        const double t = cs[j] * hcol[j] + sn[j] * hcol[j + 1];
+        hcol[j + 1] = -sn[j] * hcol[j] + cs[j] * hcol[j + 1];
+        hcol[j] = t;
+      }
+      const double d = std::hypot(hcol[k], hcol[k + 1]);
+      cs[k] = d > 0 ? hcol[k] / d : 1.0;
+      sn[k] = d > 0 ? hcol[k + 1] / d : 0.0;
+      hcol[k] = d;
+      for (int j = 0; j <= k; ++j) H[(size_t)j * m + k] = hcol[j];
+      g[k + 1] = -sn[k] * g[k];
+      g[k] = cs[k] * g[k];
+      k_used = k + 1;
+      if (std::fabs(g[k + 1]) <= tol * bnorm || nmv >= max_matvec || hn == 0) break;
+    }
+    for (int i = k_used - 1; i >= 0; --i) {
+      double sum = g[i];
+      for (int j = i + 1; j < k_used; ++j) sum -= H[(size_t)i * m + j] * yk[j];
+      yk[i] = sum / H[(size_t)i * m + i];
+    }
+    TS_CUDA(cudaMemcpyAsync(tr->h, yk.data(), k_used * sizeof(double), cudaMemcpyHostToDevice, st));
+    if (krylov_combine(tr->w, tr->basis, n, k_used, tr->h, n, st)) return fail(TS_ERR_CUDA, "combine");
+    if (vec_axpy(tr->dphi, tr->w, 1.0, n, st)) return fail(TS_ERR_CUDA, "axpy");
+    // true linear residual: r(phi0) + A d = r(phi0 + d) (the operator is linear)
+    if (vec_axpy(phi, tr->dphi, 1.0, n, st)) return fail(TS_ERR_CUDA, "axpy");
+    TS_TRY(tracer_apply<double, N>(tr, phi, tr->w, st));
+    ++nmv;
+    beta = tracer_dnorm(tr, tr->w, n, st, &rc);
+    if (rc) return fail(TS_ERR_CUDA, "tracer solve: norm");
+    if (vec_axpy(phi, tr->dphi, -1.0, n, st)) return fail(TS_ERR_CUDA, "axpy");
+    *rel = beta / bnorm;
+    if (beta <= tol * bnorm || nmv >= max_matvec) break;
+  }
+  if (vec_axpy(phi, tr->dphi, 1.0, n, st)) return fail(TS_ERR_CUDA, "axpy");
+  TS_CUDA(cudaStreamSynchronize(st));
+  *matvecs = nmv;
+  if (*rel > tol) return fail(TS_ERR_NOCONV, "ts_tracer_solve: matvec cap reached");
   return 0;
 }
 
@@ -1531,6 +1654,12 @@ int ts_tracer_create(const ts_mesh* mesh, int N, double kappa, double omega, dou
 
 void ts_tracer_free(ts_tracer* t) {
   if (!t) return;
+  dfree(t->basis);
+  dfree(t->w);
+  dfree(t->r);
+  dfree(t->dphi);
+  dfree(t->partial);
+  dfree(t->h);
   dfree(t->d_dmask);
   dfree(t->d_counter);
   dfree(t->a4_64);
@@ -1550,6 +1679,26 @@ int ts_tracer_set_dirichlet(ts_tracer* t, int tag) {
       for (int k = 0; k < 3; ++k) t->dmask[m->bfaces[3 * f + k]] = 1;
   t->dirty = true;
   return 0;
+}
+
+int ts_tracer_set_stabilised(ts_tracer* t, int gls) {
+  if (!t) return fail(TS_ERR_ARG, "NULL tracer");
+  if (gls != 0 && gls != 1) return fail(TS_ERR_ARG, "ts_tracer_set_stabilised: 0 or 1");
+  t->gls = gls;
+  return 0;
+}
+
+int ts_tracer_solve(ts_tracer* t, const double* a, double* phi_inout, double tol, int krylov, int max_matvec,
+                    int* matvecs_out, double* rel_out, void* stream) {
+  if (!t || !a || !phi_inout || !matvecs_out || !rel_out) return fail(TS_ERR_ARG, "ts_tracer_solve: NULL argument");
+  if (!(tol > 0) || krylov < 1 || krylov > 128 || max_matvec < 1)
+    return fail(TS_ERR_ARG, "ts_tracer_solve: tol > 0, 1 <= krylov <= 128, max_matvec >= 1");
+  if (t->dirty) {
+    TS_CUDA(cudaMemcpy(t->d_dmask, t->dmask.data(), t->dmask.size(), cudaMemcpyHostToDevice));
+    t->dirty = false;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  TS_DISPATCH(t->N, (tracer_solve_impl<NN>(t, a, phi_inout, tol, krylov, max_matvec, matvecs_out, rel_out, st)));
 }
 
 int ts_tracer_residual(ts_tracer* t, const void* a, const void* phi, void* r, int precision, void* stream) {

@@ -497,7 +497,8 @@ template <typename T, int N, typename S = T>
 __global__ void __launch_bounds__(128)
     tracer_kernel(const int4* __restrict__ tets, const S* __restrict__ geo, const S* __restrict__ a4,
                   const S* __restrict__ phi, const S* __restrict__ tau, const uint8_t* __restrict__ dmask,
-                  S* __restrict__ out, const S* __restrict__ dft, T kappa, T omega, int64_t e0, int64_t e1) {
+                  S* __restrict__ out, const S* __restrict__ dft, T kappa, T omega, int64_t e0, int64_t e1,
+                  int gls) {
   using D = Dims<N>;
   using L = TracerLayout<N>;
   constexpr int C = D::C, K = D::K, NM = D::NM, NT = D::NT, NTP = D::NT_PAD;
@@ -612,7 +613,7 @@ __global__ void __launch_bounds__(128)
       T acc = 0;
 #pragma unroll
       for (int kk = 0; kk < NM; ++kk) acc = mad(tr[kk], rq[stor_of(kk)], acc);
-      tq[q * C + stor_of(r)] = acc;
+      tq[q * C + stor_of(r)] = gls ? acc : T(0);   // Galerkin only: no least-squares term
     }
     for (int q = lane; q < 4; q += 32) tq[q * C + 1] = T(0);
     __syncwarp();
@@ -662,7 +663,7 @@ __global__ void __launch_bounds__(128)
 template <typename T, int N, typename S>
 static int launch_tracer_t(const int4* tets, const S* geo, const S* a4, const S* phi, const S* tau,
                            const uint8_t* dmask, S* out, const S* dft, double kappa, double omega,
-                           int64_t e0, int64_t e1, cudaStream_t st) {
+                           int64_t e0, int64_t e1, cudaStream_t st, int gls) {
   using L = TracerLayout<N>;
   if (e1 <= e0) return 0;
   int warps = 4;
@@ -674,15 +675,15 @@ static int launch_tracer_t(const int4* tets, const S* geo, const S* a4, const S*
   if (blocks > 152 * 32) blocks = 152 * 32;
   count_launches(1);
   tracer_kernel<T, N, S><<<(int)blocks, warps * 32, smem, st>>>(tets, geo, a4, phi, tau, dmask, out, dft,
-                                                                T(kappa), T(omega), e0, e1);
+                                                                T(kappa), T(omega), e0, e1, gls);
   return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
 template <typename T, int N>
 int launch_tracer(const int4* tets, const T* geo, const T* a4, const T* phi, const T* tau,
                   const uint8_t* dmask, T* out, const T* dft, double kappa, double omega, int64_t e0,
-                  int64_t e1, cudaStream_t st) {
-  return launch_tracer_t<T, N, T>(tets, geo, a4, phi, tau, dmask, out, dft, kappa, omega, e0, e1, st);
+                  int64_t e1, cudaStream_t st, int gls) {
+  return launch_tracer_t<T, N, T>(tets, geo, a4, phi, tau, dmask, out, dft, kappa, omega, e0, e1, st, gls);
 }
 
 // a [V][3][C] -> a4 [V][4][C] (the flow layout the tau kernels read; pressure zero)
@@ -709,35 +710,49 @@ template int launch_repack_velocity<double>(const double*, double*, int64_t, int
 
 // ---------------------------------------------------------------- outlets
 // One block per call: Q_c = sum_A sum_i w_Ai v[A][i][c]; out[A][i][c] += R w_Ai Q_c.
-// Warp w reduces the flow rates Q_c of the coefficients c = w, w + 16, ...
-// over the outlet nodes (shuffle reduction), then all threads scatter.
+// Thread t owns the outlet nodes t, t + blockDim, ... and keeps its partial
+// flow rates of all C coefficients in its own column of part[C][blockDim]
+// (the loads of a node are independent, so one node costs one memory round
+// trip, not one per coefficient); warp w then sums the columns of the
+// coefficients c = w, w + nw, ... in a fixed order (deterministic), and the
+// threads scatter to their own nodes.
 template <typename T>
-__global__ void __launch_bounds__(512) outlet_kernel(const int32_t* __restrict__ nodes,
+__global__ void __launch_bounds__(256) outlet_kernel(const int32_t* __restrict__ nodes,
                                                      const T* __restrict__ w, int n, T R,
                                                      const T* __restrict__ v,
                                                      const uint8_t* __restrict__ dmask, int mask_input,
                                                      T* __restrict__ out, int C) {
-  __shared__ T Q[128];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  extern __shared__ __align__(16) unsigned char outlet_smem[];
+  T* part = reinterpret_cast<T*>(outlet_smem);   // [C][blockDim.x]
+  T* Q = part + (int64_t)C * blockDim.x;         // [C]
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+  for (int c = 0; c < C; ++c) part[c * nt + tid] = T(0);
+  for (int b = tid; b < n; b += nt) {
+    const int A = nodes[b];
+    if (mask_input && dmask[A]) continue;
+    const T w0 = w[b * 3 + 0], w1 = w[b * 3 + 1], w2 = w[b * 3 + 2];
+    const T* va = v + (int64_t)A * 4 * C;
+    for (int c = 0; c < C; ++c) part[c * nt + tid] += w0 * va[c] + w1 * va[C + c] + w2 * va[2 * C + c];
+  }
+  __syncthreads();
   for (int c = warp; c < C; c += nw) {
     T acc = 0;
-    for (int b = lane; b < n; b += 32) {
-      const int A = nodes[b];
-      if (mask_input && dmask[A]) continue;
-      const T* va = v + (int64_t)A * 4 * C;
-      acc += w[b * 3 + 0] * va[0 * C + c] + w[b * 3 + 1] * va[1 * C + c] + w[b * 3 + 2] * va[2 * C + c];
-    }
+    for (int k = lane; k < nt; k += 32) acc += part[c * nt + k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) Q[c] = (c == 1) ? T(0) : acc;
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < n * 3 * C; t += blockDim.x) {
-    const int b = t / (3 * C), r = t - b * 3 * C;
-    const int i = r / C, c = r - i * C;
+  for (int b = tid; b < n; b += nt) {
     const int A = nodes[b];
-    if (dmask[A] || c == 1) continue;
-    out[(int64_t)A * 4 * C + i * C + c] += R * w[b * 3 + i] * Q[c];
+    if (dmask[A]) continue;
+    T* oa = out + (int64_t)A * 4 * C;
+    for (int i = 0; i < 3; ++i) {
+      const T s = R * w[b * 3 + i];
+      for (int c = 0; c < C; ++c)
+        if (c != 1) oa[i * C + c] += s * Q[c];
+    }
   }
 }
 
@@ -746,8 +761,14 @@ int launch_outlet(const int32_t* nodes, const T* w, int n_nodes, T R, const T* v
                   const uint8_t* dmask, int mask_input, T* out, int C, cudaStream_t st) {
   if (n_nodes <= 0) return 0;
   if (C > 128) return -1;
+  const int threads = 256;
+  const size_t smem = ((size_t)C * threads + C) * sizeof(T);
+  if (smem > 227 * 1024) return -1;
+  if (smem > 48 * 1024 &&
+      cudaFuncSetAttribute(outlet_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return -2;
   count_launches(1);
-  outlet_kernel<T><<<1, 512, 0, st>>>(nodes, w, n_nodes, R, v, dmask, mask_input, out, C);
+  outlet_kernel<T><<<1, threads, smem, st>>>(nodes, w, n_nodes, R, v, dmask, mask_input, out, C);
   return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
@@ -794,7 +815,7 @@ TS_FOR_EACH_N(TS_INST_APPLY, double)
 TS_FOR_EACH_N(TS_INST_APPLY_DD, double)
 #define TS_INST_TRACER(T, N)                                                                        \
   template int launch_tracer<T, N>(const int4*, const T*, const T*, const T*, const T*, const uint8_t*, \
-                                   T*, const T*, double, double, int64_t, int64_t, cudaStream_t);
+                                   T*, const T*, double, double, int64_t, int64_t, cudaStream_t, int);
 TS_FOR_EACH_N(TS_INST_TRACER, float)
 TS_FOR_EACH_N(TS_INST_TRACER, double)
 

@@ -320,7 +320,13 @@ __global__ void __launch_bounds__(256)
 // records: for each node A of the colour (rows[0..n_rows)),
 //   z_A = Binv_A (r_A - sum_{B != A} H_AB z_B)
 // with z read as it stands (earlier colours of this sweep already updated).
-// Binv: inverted nodal diagonal blocks, column-major (precond.cu).
+// Binv: inverted nodal diagonal blocks, column-major (precond.cu).  One warp
+// per row.  A colour holds only a few thousand rows (a few warps per SM), so
+// each warp keeps SGS_STAGES - 1 connections in flight: a ring of
+// SGS_STAGES shared-memory slots, each one record plus z_B, filled by
+// asynchronous copies while the oldest slot is multiplied.
+constexpr int SGS_STAGES = 4;
+
 template <int N>
 __global__ void __launch_bounds__(256)
     sgs_colour_kernel(const int32_t* __restrict__ rows, int64_t n_rows, const int32_t* __restrict__ row_off,
@@ -328,28 +334,57 @@ __global__ void __launch_bounds__(256)
                       const float* __restrict__ binv, const uint8_t* __restrict__ dmask,
                       const float* __restrict__ r, float* __restrict__ z) {
   using L = AsmLayout<N>;
-  constexpr int C = L::C, CC = L::CC, HB = L::HB, NB = 4 * C;
+  constexpr int C = L::C, CC = L::CC, HB = L::HB, NB = 4 * C, S = SGS_STAGES;
   constexpr int R = (NB + 31) / 32;
   extern __shared__ __align__(16) float smem_f[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
-  float* rec = smem_f + warp * L::PWARP;
-  float* xs = rec + HB;
+  float* buf0 = smem_f + warp * S * L::PWARP;   // [S][HB + NB]
   for (int64_t k = (int64_t)blockIdx.x * wpb + warp; k < n_rows; k += (int64_t)gridDim.x * wpb) {
     const int A = rows[k];
     float acc[R];
 #pragma unroll
     for (int j = 0; j < R; ++j) acc[j] = 0.f;
-    for (int p = row_off[A]; p < row_off[A + 1]; ++p) {
-      const int B = cols[p];
-      if (B == A) continue;
-      const float4* src = reinterpret_cast<const float4*>(H + (int64_t)p * HB);
-      for (int t = lane; t < HB / 4; t += 32) reinterpret_cast<float4*>(rec)[t] = __ldg(src + t);
-      const bool dirB = dmask[B] != 0;
+    const int r0 = row_off[A], r1 = row_off[A + 1];
+    // position of the diagonal connection in the row (rows hold at most a
+    // few dozen connections): the i-th off-diagonal one is r0 + i, or
+    // r0 + i + 1 from the diagonal on
+    int pd = r1;
+    for (int b = r0; b < r1; b += 32) {
+      const unsigned hit = __ballot_sync(0xffffffffu, b + lane < r1 && cols[b + lane] == A);
+      if (hit) {
+        pd = b + __ffs(hit) - 1;
+        break;
+      }
+    }
+    const int n_off = (r1 - r0) - (pd < r1 ? 1 : 0);
+    auto conn = [&](int i) { return r0 + i + (r0 + i >= pd ? 1 : 0); };
+    // one commit group per ring position, empty past the row's end, so that
+    // waiting for all but the newest S - 1 groups always means "slot i landed"
+    auto stage = [&](int i) {
+      if (i < n_off) {
+        const int p = conn(i);
+        float* dst = buf0 + (i % S) * L::PWARP;
+        const float4* src = reinterpret_cast<const float4*>(H + (int64_t)p * HB);
+        for (int t = lane; t < HB / 4; t += 32) cp_async16(dst + 4 * t, src + t);
+        const float4* zb = reinterpret_cast<const float4*>(z + (int64_t)cols[p] * NB);
+        for (int t = lane; t < NB / 4; t += 32) cp_async16(dst + HB + 4 * t, zb + t);
+      }
+      cp_async_commit();
+    };
+#pragma unroll
+    for (int i = 0; i < S - 1; ++i) stage(i);
+    for (int i = 0; i < n_off; ++i) {
+      // slot (i + S - 1) % S was multiplied in iteration i - 1 (synced below)
+      stage(i + S - 1);
+      cp_async_wait<S - 1>();
+      __syncwarp();
+      float* rec = buf0 + (i % S) * L::PWARP;
+      float* xs = rec + HB;
+      const bool dirB = dmask[cols[conn(i)]] != 0;
       for (int t = lane; t < NB; t += 32) {
         const int f = t / C, c = t - f * C;
-        const float v = z[(int64_t)B * NB + t];
-        xs[t] = (c == 1 || (dirB && f < 3)) ? 0.f : v;
+        if (c == 1 || (dirB && f < 3)) xs[t] = 0.f;
       }
       __syncwarp();
 #pragma unroll
@@ -359,16 +394,22 @@ __global__ void __launch_bounds__(256)
           const int f = o / C, rr = o - f * C;
           float s = acc[j];
           if (f < 3) {
-            const float* Kr = rec + rr * C;
-            const float* xi = xs + f * C;
+            const float2* Kr = reinterpret_cast<const float2*>(rec + rr * C);
+            const float2* xi = reinterpret_cast<const float2*>(xs + f * C);
 #pragma unroll
-            for (int c = 0; c < C; ++c) s = fmaf(Kr[c], xi[c], s);
+            for (int c = 0; c < C / 2; ++c) {
+              const float2 a = Kr[c], b = xi[c];
+              s = fmaf(a.x, b.x, fmaf(a.y, b.y, s));
+            }
             s = fmaf(rec[2 * CC + f], xs[3 * C + rr], s);
           } else {
-            const float* Lr = rec + CC + rr * C;
-            const float* xp = xs + 3 * C;
+            const float2* Lr = reinterpret_cast<const float2*>(rec + CC + rr * C);
+            const float2* xp = reinterpret_cast<const float2*>(xs + 3 * C);
 #pragma unroll
-            for (int c = 0; c < C; ++c) s = fmaf(Lr[c], xp[c], s);
+            for (int c = 0; c < C / 2; ++c) {
+              const float2 a = Lr[c], b = xp[c];
+              s = fmaf(a.x, b.x, fmaf(a.y, b.y, s));
+            }
             s = fmaf(rec[2 * CC + 3], xs[rr], s);
             s = fmaf(rec[2 * CC + 4], xs[C + rr], s);
             s = fmaf(rec[2 * CC + 5], xs[2 * C + rr], s);
@@ -378,14 +419,18 @@ __global__ void __launch_bounds__(256)
       }
       __syncwarp();
     }
-    // t = r_A - (off-diagonal sum), then z_A = Binv_A t
+    // the groups still open are empty (positions past the row's end)
+    cp_async_wait<0>();
+    __syncwarp();
+    // t = r_A - (off-diagonal sum) into the first buffer's x slot, then z_A = Binv_A t
+    float* tv = buf0 + HB;
     const bool dirA = dmask[A] != 0;
 #pragma unroll
     for (int j = 0; j < R; ++j) {
       const int o = lane + 32 * j;
       if (o < NB) {
         const int f = o / C, c = o - f * C;
-        xs[o] = (c == 1 || (dirA && f < 3)) ? 0.f : r[(int64_t)A * NB + o] - acc[j];
+        tv[o] = (c == 1 || (dirA && f < 3)) ? 0.f : r[(int64_t)A * NB + o] - acc[j];
       }
     }
     __syncwarp();
@@ -394,7 +439,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int j = 0; j < R; ++j) out[j] = 0.f;
     for (int col = 0; col < NB; ++col) {
-      const float xc = xs[col];
+      const float xc = tv[col];
 #pragma unroll
       for (int j = 0; j < R; ++j) {
         const int o = lane + 32 * j;
@@ -416,8 +461,9 @@ int launch_sgs_colour(const int32_t* rows, int64_t n_rows, const int32_t* row_of
                       cudaStream_t st) {
   using L = AsmLayout<N>;
   if (n_rows <= 0) return 0;
-  const int warps = 8;
-  const size_t smem = (size_t)warps * L::PWARP * sizeof(float);
+  int warps = 8;
+  while (warps > 1 && (size_t)warps * SGS_STAGES * L::PWARP * sizeof(float) > 200 * 1024) --warps;
+  const size_t smem = (size_t)warps * SGS_STAGES * L::PWARP * sizeof(float);
   if (smem > 227 * 1024) return -6;
   cudaFuncSetAttribute(sgs_colour_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int64_t blocks = (n_rows + warps - 1) / warps;

@@ -72,7 +72,7 @@ int launch_apply_dd(int mode, const int4* tets, const double* geo, const double*
 template <typename T, int N>
 int launch_tracer(const int4* tets, const T* geo, const T* a4, const T* phi, const T* tau,
                   const uint8_t* dmask, T* out, const T* dft, double kappa, double omega, int64_t e0,
-                  int64_t e1, cudaStream_t st);
+                  int64_t e1, cudaStream_t st, int gls = 1);
 template <typename T>
 int launch_repack_velocity(const T* a, T* a4, int64_t V, int C, cudaStream_t st);
 

@@ -64,3 +64,43 @@ def test_tracer_residual_matches_oracle(name, prec):
         assert rel_l2(r12, r1 + 2 * r2) <= 1e-13
     t.close()
     ts.ts_mesh_free(m)
+
+
+def test_tracer_solve_reaches_the_oracle_root_and_gls_bounds_the_step():
+    # a step of tracer entering a pipe with a pulsating axial velocity at a cell
+    # Peclet number near 50: the GLS solution is the root of the oracle's
+    # residual, every mode is energised by the coupling (section 3.3), and it
+    # stays near [0, 1] where the Galerkin-only method over- and undershoots
+    import torch
+    import paper_2311_09465_gb300 as ts
+    mesh = mg.pipe(nc=3, nr=2, nz=12, seed=4)
+    N, kappa, omega = 4, 0.004, 1.2
+    V = mesh.n_nodes
+    a = np.zeros((V, 3, N, 2))
+    a[:, 2, 0, 0] = 1.0
+    a[:, 2, 1, 0] = 0.3
+    inlet = cases.nodes_with_tag(mesh, mg.TAG_INLET1)
+    phi0 = np.zeros((V, N, 2))
+    phi0[inlet & (mesh.xyz[:, 0] > 0), 0, 0] = 1.0
+    m = ts.ts_mesh_load(mesh.xyz, mesh.tets, mesh.bfaces, mesh.btag)
+    out = {}
+    for gls in (True, False):
+        t = ts.Tracer(m, V, N, kappa, omega, 3.0, dirichlet_tags=(mg.TAG_INLET1,))
+        t.stabilised(gls)
+        phi = to_dev(phi0, torch.float64)
+        rep = t.solve(to_dev(a, torch.float64), phi, tol=1e-10, krylov=100, max_matvec=20000)
+        assert rep["rel"] <= 1e-10, rep
+        out[gls] = to_np(phi)
+        t.close()
+    ts.ts_mesh_free(m)
+    tp = tr.make_tracer_problem(mesh.xyz, mesh.tets, N, kappa, omega, inlet, 3.0)
+    r0 = np.linalg.norm(tr.tracer_residual(tp, a, phi0))
+    assert np.linalg.norm(tr.tracer_residual(tp, a, out[True])) <= 1e-8 * r0
+    # the inlet data stay, Im(mode 0) stays zero, the pulsation energises the higher modes
+    np.testing.assert_array_equal(out[True][inlet], phi0[inlet])
+    assert np.all(out[True][:, 0, 1] == 0)
+    assert np.abs(out[True][:, 1:]).max() > 1e-3
+    # boundedness of the mean (mode 0) field: GLS near [0, 1], Galerkin worse
+    over = {g: max(out[g][:, 0, 0].max() - 1.0, -out[g][:, 0, 0].min()) for g in out}
+    assert over[True] < 0.15, over
+    assert over[False] > over[True], over
