@@ -904,8 +904,9 @@ def run_mode_study(args, Ns=(2, 3, 5, 7, 10), N_ref=15, h=0.3, Re=100.0, Wo=10.0
 
 def run_assembled(args, R=20):
     """The assembled block-structured tangent of the paper's variant (section
-    2.5.2) on the bench junction: assembly time, storage, and the SpMV against
-    the matrix-free product of the same variant (CUDA events, one JSON line).
+    2.5.2) on the bench junction: assembly time, storage, the SpMV against
+    the matrix-free product of the same variant, and the block preconditioners
+    built on it (set-up and application; CUDA events, one JSON line).
     HBM roofline of the SpMV: the records, their column ids and row offsets,
     x and Hv once each, against the measured copy bandwidth."""
     import torch
@@ -945,11 +946,44 @@ def run_assembled(args, R=20):
     V, N, E = case.mesh.n_nodes, case.N, case.mesh.n_tets
     alg = rec + 4 * nnz + 4 * (V + 1) + 2 * V * 8 * N * 4
     peak, peak_kind = _peaks()
+    # the block preconditioners on their own: set-up and one application
+    # (x: an FP64 field; Gauss-Seidel: forward + backward colour sweeps)
+    x64 = v.double()
+    z64 = torch.empty_like(x64)
+    prec = {}
+    for kind, name in ((2, "block_jacobi"), (3, "block_gauss_seidel")):
+        g.precond_setup(kind)
+        ev[0].record()
+        g.precond_setup(kind)
+        ev[1].record()
+        torch.cuda.synchronize()
+        t_set = ev[0].elapsed_time(ev[1]) / 1e3
+        for _ in range(3):
+            g.precond_apply(kind, x64, z64)
+        ev[0].record()
+        for _ in range(R):
+            g.precond_apply(kind, x64, z64)
+        ev[1].record()
+        torch.cuda.synchronize()
+        prec[name] = {"setup_ms": t_set * 1e3, "apply_ms": ev[0].elapsed_time(ev[1]) / R}
+    # one Gauss-Seidel sweep reads every off-diagonal record with its column
+    # id, the row offsets, the inverted blocks and r once, and writes z once;
+    # the application is two sweeps plus the FP64 <-> FP32 conversions
+    nf = V * 8 * N
+    nb2 = (8 * N) ** 2 * 4
+    sweep = (nnz - V) * (rec // nnz) + 4 * nnz + 4 * (V + 1) + V * nb2 + 2 * 4 * nf
+    alg_sgs = 2 * sweep + (8 + 4) * nf + 4 * nf + (4 + 8) * nf
+    t_sgs = prec["block_gauss_seidel"]["apply_ms"] / 1e3
+    prec["block_gauss_seidel"]["roofline"] = {
+        "bound": "hbm", "achieved": alg_sgs / t_sgs / 1e9, "peak": peak, "unit": "GB/s",
+        "frac": alg_sgs / t_sgs / 1e9 / peak, "algorithmic_bytes": alg_sgs, "peak_source": peak_kind,
+        "colours": ts.ts_mesh_node_colours(g.mesh)}
     out = {"assembled": "paper-variant tangent, block-structured (section 2.5.2)",
            "workload": f"junction {E} tets, N={N}", "connections": nnz, "record_bytes": rec,
            "assembly_ms": t_asm * 1e3, "spmv_ms": t_spmv * 1e3, "matrix_free_paper_ms": t_mf * 1e3,
            "spmv_element_mode_evals_per_s": E * N / t_spmv,
            "rel_l2_spmv_vs_matrix_free": float((hv - hm).norm() / hm.norm()),
+           "preconditioners": prec,
            "roofline": {"bound": "hbm", "achieved": alg / t_spmv / 1e9, "peak": peak, "unit": "GB/s",
                         "frac": alg / t_spmv / 1e9 / peak, "algorithmic_bytes": alg, "peak_source": peak_kind}}
     print(json.dumps(out), flush=True)

@@ -158,6 +158,12 @@ int  ts_mesh_load(const double* xyz_host, int64_t n_nodes, const int32_t* tets_h
 void ts_mesh_free(ts_mesh* mesh);
 /* number of element colours of a loaded mesh (or negative error) */
 int  ts_mesh_colors(const ts_mesh* mesh);
+/* Colouring of the node graph of a loaded mesh: two nodes of one colour never
+ * share an element.  Returns the number of colours (or a negative error) and,
+ * when colour_host (host, n_nodes int32) is not NULL, writes each node's
+ * colour there.  The block Gauss-Seidel preconditioner (ts_precond_apply kind
+ * 3) sweeps the colours in this numbering. */
+int  ts_mesh_node_colours(const ts_mesh* mesh, int32_t* colour_host);
 
 /* Creates a problem (physics + boundary conditions) on a mesh.  The mesh must
  * outlive the problem.  TS_ERR_UNSUPPORTED if no kernel is compiled for N. */
@@ -300,6 +306,31 @@ int64_t ts_mesh_connections(const ts_mesh* mesh);
  * TS_ERR_ARG if no residual was computed yet.  A block that cannot be inverted
  * is stored as the identity. */
 int  ts_block_diagonal(ts_problem* prob, float* blocks, int invert, void* stream);
+
+/* The block preconditioners of ts_solve on their own (precond 2 and 3 of
+ * ts_solve_opts), for use in another solver or to time them.
+ * ts_precond_setup builds, at the state of the last ts_residual call,
+ *   kind 2, nodal block Jacobi: B_A^{-1}, the inverted diagonal blocks of
+ *           ts_block_diagonal (fixed unknowns: identity rows and columns);
+ *   kind 3, symmetric block Gauss-Seidel: the same inverted blocks on the
+ *           diagonal and the assembled paper-variant blocks H_AB of ts_assemble
+ *           (section 2.5.2) off it (the resistance outlets' coupling between
+ *           different nodes is left out; a node's own coupling is in B_A).
+ * ts_precond_apply computes z = P^{-1} x (x, z: device, double, the field
+ * layout, distinct):
+ *   kind 2: z_A = B_A^{-1} x_A for every node A;
+ *   kind 3: from z = 0, a forward sweep over the node colours of
+ *           ts_mesh_node_colours in increasing order, then a backward sweep in
+ *           decreasing order, each updating every node A of a colour (no two
+ *           of which are coupled) as z_A = B_A^{-1} (x_A - sum_{B != A} H_AB z_B)
+ *           with the z of the colours already visited; Dirichlet velocity
+ *           entries and Im(mode 0) of x are ignored and the same entries of z
+ *           are zero.  Computed in FP32 (x rounded), returned in FP64.
+ * TS_ERR_ARG: no residual yet, kind not 2 or 3, apply before the setup of that
+ * kind at the current state (a new ts_residual invalidates both), x == z.
+ * TS_ERR_UNSUPPORTED (kind 3) with backflow faces. */
+int  ts_precond_setup(ts_problem* prob, int kind, void* stream);
+int  ts_precond_apply(ts_problem* prob, int kind, const double* x, double* z, void* stream);
 
 /* Tangent product Hv (eq. K_mat, variant from the problem) at the state of
  * the last ts_residual call, plus c1 rho / dt_pseudo M v on the momentum rows

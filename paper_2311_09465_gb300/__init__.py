@@ -81,6 +81,7 @@ def lib() -> ctypes.CDLL:
     L.ts_mesh_free.argtypes = [vp]
     L.ts_mesh_free.restype = None
     L.ts_mesh_colors.argtypes = [vp]
+    L.ts_mesh_node_colours.argtypes = [vp, i32p]
     L.ts_problem_create.argtypes = [vp, ctypes.POINTER(ts_params), ctypes.POINTER(vp)]
     L.ts_problem_free.argtypes = [vp]
     L.ts_problem_free.restype = None
@@ -93,6 +94,8 @@ def lib() -> ctypes.CDLL:
     L.ts_residual.argtypes = [vp, vp, vp, ctypes.c_int, vp]
     L.ts_jvp.argtypes = [vp, vp, vp, ctypes.c_int, vp]
     L.ts_block_diagonal.argtypes = [vp, vp, ctypes.c_int, vp]
+    L.ts_precond_setup.argtypes = [vp, ctypes.c_int, vp]
+    L.ts_precond_apply.argtypes = [vp, ctypes.c_int, vp, vp, vp]
     L.ts_assemble.argtypes = [vp, vp]
     L.ts_spmv.argtypes = [vp, vp, vp, vp]
     L.ts_assembled_bytes.argtypes = [vp]
@@ -214,6 +217,20 @@ def ts_mesh_colors(mesh) -> int:
     return n
 
 
+def ts_mesh_node_colours(mesh, n_nodes=None):
+    """Number of node colours; with n_nodes, also each node's colour (int32 array)."""
+    if n_nodes is None:
+        n = lib().ts_mesh_node_colours(mesh, None)
+        if n < 0:
+            _check(n)
+        return n
+    out = np.zeros(int(n_nodes), dtype=np.int32)
+    n = lib().ts_mesh_node_colours(mesh, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    if n < 0:
+        _check(n)
+    return n, out
+
+
 def ts_problem_create(mesh, params: ts_params):
     out = ctypes.c_void_p()
     _check(lib().ts_problem_create(mesh, ctypes.byref(params), ctypes.byref(out)))
@@ -294,6 +311,23 @@ def ts_block_diagonal(prob, out, invert=False, stream=None):
     _check(lib().ts_block_diagonal(prob, ctypes.c_void_p(out.data_ptr()), int(bool(invert)),
                                    _stream_ptr(stream)))
     return out
+
+
+def ts_precond_setup(prob, kind, stream=None):
+    """Builds the block preconditioner kind 2 (block Jacobi) or 3 (symmetric
+    block Gauss-Seidel) at the state of the last residual."""
+    _check(lib().ts_precond_setup(prob, int(kind), _stream_ptr(stream)))
+
+
+def ts_precond_apply(prob, kind, x, z, stream=None):
+    """z = P^{-1} x with the preconditioner last built for kind (CUDA float64 fields)."""
+    import torch
+    for t in (x, z):
+        if not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+            raise ValueError("x and z must be contiguous CUDA float64 tensors")
+    _check(lib().ts_precond_apply(prob, int(kind), ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(z.data_ptr()),
+                                  _stream_ptr(stream)))
+    return z
 
 
 def ts_assemble(prob, stream=None):
@@ -383,6 +417,17 @@ class GLSProblem:
 
     def colors(self):
         return ts_mesh_colors(self.mesh)
+
+    def node_colours(self):
+        """(number of node colours, each node's colour)."""
+        return ts_mesh_node_colours(self.mesh, self.n_nodes)
+
+    def precond_setup(self, kind, stream=None):
+        ts_precond_setup(self.prob, kind, stream)
+
+    def precond_apply(self, kind, x, z=None, stream=None):
+        z = self.field(x.dtype, x.device) if z is None else z
+        return ts_precond_apply(self.prob, kind, x, z, stream)
 
     def field(self, dtype, device="cuda"):
         import torch

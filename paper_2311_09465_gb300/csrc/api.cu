@@ -59,6 +59,7 @@ struct ts_mesh {
   int64_t nnzb = 0;                   // node-graph connections (A itself included)
   int32_t* d_row_off = nullptr;       // [V + 1] node graph in CSR
   int32_t* d_cols = nullptr;          // [nnzb] sorted neighbour ids per row
+  std::vector<int32_t> node_colour;   // colour of each node (host)
   std::vector<int64_t> ncolour_off;   // node colouring of the node graph: colour c holds
   int32_t* d_node_perm = nullptr;     // d_node_perm[ncolour_off[c] .. ncolour_off[c+1])
 };
@@ -130,6 +131,7 @@ struct ts_problem {
   float *d_v32 = nullptr, *d_w32 = nullptr;
   double *d_D = nullptr, *d_t = nullptr;      // preconditioner diagonal (inverted), temp
   float* d_binv = nullptr;                    // inverted nodal blocks [V][8N][8N] (block Jacobi)
+  bool binv_valid = false;                    // d_binv built at the current linearisation state
   float* d_eig = nullptr;                     // eigenpairs of M per point [E*4][EIG] (exact tangent)
   float* d_dT = nullptr;                      // d tau[v] L(u0) per point [E][4][3][C] (exact tangent)
   float* d_hasm = nullptr;                    // assembled PAPER tangent records [nnzb][2C^2 + 8]
@@ -394,6 +396,7 @@ static int residual_impl(ts_problem* pr, const T* y, T* r, cudaStream_t st) {
   l.valid = true;
   l.exact_valid = exact;
   pr->hasm_valid = false;
+  pr->binv_valid = false;
   // the other precision's state is now stale
   if (sizeof(T) == 4) pr->l64.valid = false; else pr->l32.valid = false;
   return 0;
@@ -622,7 +625,9 @@ static int block_apply_any(ts_problem* pr, const double* x, double* z, cudaStrea
 static int block_precond_setup(ts_problem* pr, cudaStream_t st) {
   const int64_t nb = 8 * (int64_t)pr->p.N;
   if (!pr->d_binv) TS_TRY(dalloc(&pr->d_binv, (size_t)pr->mesh->V * nb * nb));
-  return block_diag_any(pr, 1, pr->d_binv, st);
+  TS_TRY(block_diag_any(pr, 1, pr->d_binv, st));
+  pr->binv_valid = true;
+  return 0;
 }
 
 template <typename T, int N>
@@ -930,6 +935,7 @@ int ts_mesh_load(const double* xyz_host, int64_t n_nodes, const int32_t* tets_ho
     m->ncolour_off = cnt;
     std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
     for (int64_t v = 0; v < n_nodes; ++v) perm[fill[ncl[v]]++] = (int32_t)v;
+    m->node_colour = ncl;
   }
   int rc = 0;
   rc |= dalloc(&m->d_tets, (size_t)n_tets);
@@ -1418,6 +1424,31 @@ int ts_block_diagonal(ts_problem* pr, float* blocks, int invert, void* stream) {
   if (!pr || !blocks) return fail(TS_ERR_ARG, "ts_block_diagonal: NULL argument");
   if (invert != 0 && invert != 1) return fail(TS_ERR_ARG, "ts_block_diagonal: invert must be 0 or 1");
   return block_diag_any(pr, invert, blocks, (cudaStream_t)stream);
+}
+
+int ts_mesh_node_colours(const ts_mesh* m, int32_t* colour_host) {
+  if (!m) return fail(TS_ERR_ARG, "ts_mesh_node_colours: NULL mesh");
+  if (colour_host) std::copy(m->node_colour.begin(), m->node_colour.end(), colour_host);
+  return (int)m->ncolour_off.size() - 1;
+}
+
+int ts_precond_setup(ts_problem* pr, int kind, void* stream) {
+  if (!pr) return fail(TS_ERR_ARG, "ts_precond_setup: NULL problem");
+  if (kind != 2 && kind != 3) return fail(TS_ERR_ARG, "ts_precond_setup: kind must be 2 or 3");
+  if (!pr->l32.valid && !pr->l64.valid) return fail(TS_ERR_ARG, "ts_precond_setup: no residual computed yet");
+  TS_TRY(sync_dmask(pr));
+  return kind == 2 ? block_precond_setup(pr, (cudaStream_t)stream) : sgs_setup(pr, (cudaStream_t)stream);
+}
+
+int ts_precond_apply(ts_problem* pr, int kind, const double* x, double* z, void* stream) {
+  if (!pr || !x || !z) return fail(TS_ERR_ARG, "ts_precond_apply: NULL argument");
+  if (x == z) return fail(TS_ERR_ARG, "ts_precond_apply: x and z alias");
+  if (kind != 2 && kind != 3) return fail(TS_ERR_ARG, "ts_precond_apply: kind must be 2 or 3");
+  if (!pr->binv_valid || (kind == 3 && (!pr->hasm_valid || !pr->d_r32)))
+    return fail(TS_ERR_ARG, "ts_precond_apply: preconditioner not set up at the current state");
+  TS_TRY(sync_dmask(pr));
+  const cudaStream_t st = (cudaStream_t)stream;
+  return kind == 2 ? block_apply_any(pr, x, z, st) : sgs_apply_any(pr, x, z, st);
 }
 
 int ts_jvp(ts_problem* pr, const void* v, void* hv, int precision, void* stream) {

@@ -6,6 +6,10 @@
   the pseudo-time mass, with a resistance outlet; FP32 bar 1e-5 relative L2.
 * Inverse: the stored inverse times H_AA (fixed rows and columns set to the
   identity) is the identity.
+* Applications (ts_precond_apply): block Jacobi and the forward-backward
+  block Gauss-Seidel sweeps equal the same block operations done in FP64 on
+  the oracle's dense tangent in the library's node-colour order; FP32 bar
+  1e-4 relative L2.
 * Solve: with the nodal block-Jacobi (precond 2) or the symmetric block
   Gauss-Seidel (precond 3) preconditioner the solve reaches the oracle's root
   within the converged-field bar 1e-6 (pipe: the oracle's own solve; small
@@ -83,6 +87,90 @@ def test_block_diagonal_matches_dense_tangent(name, make, variant, dt, prec):
     eye = np.eye(nb)
     worst = max(np.linalg.norm(inv[A] @ B[A] - eye) / math.sqrt(nb) for A in range(V))
     assert worst <= 1e-4, worst
+    g.close()
+
+
+def _fixed_mask(case):
+    V, N = case.mesh.n_nodes, case.N
+    fixed = np.zeros((V, 4, N, 2), dtype=bool)
+    fixed[:, :, 0, 1] = True
+    fixed[case.dirichlet_mask, 0:3] = True
+    return fixed.reshape(V, 8 * N)
+
+
+SWEEP_CASES = [
+    ("pipe_N3_paper", lambda: _pipe(3, nc=2, nr=2, nz=4), "paper", 0.8),
+    ("pipe_N3_lin_a", lambda: _pipe(3, nc=2, nr=1, nz=5), "lin_a", 0.4),
+    ("pipe_N7_lin_a", lambda: _pipe(7, nc=2, nr=1, nz=3), "lin_a", 1.3),
+]
+
+
+@pytest.mark.parametrize("name,make,variant,dt", SWEEP_CASES, ids=[c[0] for c in SWEEP_CASES])
+def test_preconditioner_applications_match_dense_block_sweeps(name, make, variant, dt):
+    """ts_precond_apply kind 2 and 3 against the same block operations on the
+    oracle's dense tangent (eq. K_mat): on the diagonal the blocks of the
+    problem's variant (FROZEN for LIN_A), off it the paper variant's
+    (section 2.5.2), the sweeps in the library's node-colour order.  No
+    resistance outlet: its coupling between different nodes is left out of
+    the Gauss-Seidel blocks by design.  FP32 bar 1e-4 relative L2."""
+    import torch
+    import paper_2311_09465_gb300 as ts
+    case = make()
+    case.resistance = {}
+    y = _state(case, seed=7, scale=0.8)
+    N, V = case.N, case.mesh.n_nodes
+    nb = 8 * N
+    prob = op.problem_from_case(case)
+    lin = op.linearize(prob, y)
+    mc = mass_coef(case, dt)
+    Hd = sv.dense_matrix(prob, lin, "paper" if variant == "paper" else "frozen", mc).reshape(V, nb, V, nb)
+    Hp = sv.dense_matrix(prob, lin, "paper", mc).reshape(V, nb, V, nb)
+    fixed = _fixed_mask(case)
+    Dinv = np.empty((V, nb, nb))
+    for A in range(V):
+        B = Hd[A, :, A, :].copy()
+        B[fixed[A], :] = 0.0
+        B[:, fixed[A]] = 0.0
+        B[fixed[A], fixed[A]] = 1.0
+        Dinv[A] = np.linalg.inv(B)
+    off = Hp.copy()
+    for A in range(V):
+        off[A, fixed[A], :, :] = 0.0
+        off[:, :, A, fixed[A]] = 0.0
+        off[A, :, A, :] = 0.0
+    x = cases.random_state(case.mesh, N, seed=8).reshape(V, nb)
+    x[fixed] = 0.0
+
+    g = ts.GLSProblem(case, variant=variant, dt_pseudo=dt)
+    g.residual(to_dev(y, torch.float64))
+    xd = to_dev(x.reshape(V, 4, N, 2), torch.float64)
+    with pytest.raises(ts.TsError):
+        g.precond_apply(3, xd)
+    # block Jacobi
+    g.precond_setup(2)
+    zj = to_np(g.precond_apply(2, xd)).reshape(V, nb)
+    ref_j = np.einsum("aij,aj->ai", Dinv, x)
+    assert rel_l2(zj, ref_j) <= 1e-4, rel_l2(zj, ref_j)
+    # symmetric block Gauss-Seidel over the node colours
+    g.precond_setup(3)
+    zs = to_np(g.precond_apply(3, xd)).reshape(V, nb)
+    n_col, colour = g.node_colours()
+    assert colour.shape == (V,) and colour.min() == 0 and colour.max() == n_col - 1
+    for A in range(V):   # a colour holds no two nodes of one element
+        nbrs = np.nonzero(np.abs(Hp[A]).sum(axis=(0, 2)) > 0)[0]
+        assert all(colour[B] != colour[A] for B in nbrs if B != A)
+    z = np.zeros((V, nb))
+    for order in (range(n_col), range(n_col - 1, -1, -1)):
+        for c in order:
+            nodes = np.nonzero(colour == c)[0]
+            t = x[nodes] - np.einsum("aibj,bj->ai", off[nodes], z)
+            z[nodes] = np.einsum("aij,aj->ai", Dinv[nodes], t)
+    assert rel_l2(zs, z) <= 1e-4, rel_l2(zs, z)
+    assert np.all(zs[fixed] == 0.0)
+    # a new residual invalidates both
+    g.residual(to_dev(y, torch.float64))
+    with pytest.raises(ts.TsError):
+        g.precond_apply(2, xd)
     g.close()
 
 
