@@ -68,22 +68,45 @@ __device__ bool jacobi_group(T* M, T* Vv, int k, int g, int lane, bool live, T* 
         }
       }
       __syncwarp();
+      // each rotation reads the two rows (columns) into registers before it
+      // writes any of them back: the loads of a lane are then independent and
+      // in flight together (a load after a store to the same array would have
+      // to wait for it)
       if (live && s != T(0)) {
+        T mp[NP], mq[NP];
+#pragma unroll
         for (int j = 0; j < NP; ++j) {
-          T mp = M[p * LD + j], mq = M[qq * LD + j];
-          M[p * LD + j] = c * mp - s * mq;
-          M[qq * LD + j] = s * mp + c * mq;
+          mp[j] = M[p * LD + j];
+          mq[j] = M[qq * LD + j];
+        }
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+          M[p * LD + j] = c * mp[j] - s * mq[j];
+          M[qq * LD + j] = s * mp[j] + c * mq[j];
         }
       }
       __syncwarp();
       if (live && s != T(0)) {
+        T ap[NP], aq[NP];
+#pragma unroll
         for (int i = 0; i < NP; ++i) {
-          T mp = M[i * LD + p], mq = M[i * LD + qq];
-          M[i * LD + p] = c * mp - s * mq;
-          M[i * LD + qq] = s * mp + c * mq;
-          T vp = Vv[i * LD + p], vq = Vv[i * LD + qq];
-          Vv[i * LD + p] = c * vp - s * vq;
-          Vv[i * LD + qq] = s * vp + c * vq;
+          ap[i] = M[i * LD + p];
+          aq[i] = M[i * LD + qq];
+        }
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+          M[i * LD + p] = c * ap[i] - s * aq[i];
+          M[i * LD + qq] = s * ap[i] + c * aq[i];
+        }
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+          ap[i] = Vv[i * LD + p];
+          aq[i] = Vv[i * LD + qq];
+        }
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+          Vv[i * LD + p] = c * ap[i] - s * aq[i];
+          Vv[i * LD + qq] = s * ap[i] + c * aq[i];
         }
         M[p * LD + qq] = T(0);
         M[qq * LD + p] = T(0);

@@ -49,6 +49,49 @@ __device__ __forceinline__ dd conv_entry_dd(const dd* a, int r, int s) {
   return dd_add(ar(m - n), dd_neg(ar(m + n)));
 }
 
+// (r, s), r <= s, of the packed row-major upper-triangle index t of an
+// n x n symmetric matrix (the inverse of packed_index)
+template <int NM>
+__device__ __forceinline__ void tri_rs(int t, int& r, int& s) {
+  r = 0;
+  while (t >= NM - r) {
+    t -= NM - r;
+    ++r;
+  }
+  s = r + t;
+}
+
+// The double-float multiply-add is a chain of about ten dependent FP32
+// operations, and the point's shared footprint leaves only a few warps per
+// SM, so one accumulation per lane leaves the FP32 pipe idle most of the
+// time.  Each lane therefore computes three outputs of a phase at once (t,
+// t + N, t + 2N of its group's outputs; a slot past the phase's end repeats
+// t and is not stored), three independent chains.  Within an output the
+// terms are added in the same order as a plain loop would, so the results
+// do not depend on this grouping.
+struct Dot3 {
+  dd c0, c1, c2;
+};
+
+// c_x += sum_j a_x[j * as] b_x[j * bs], j = 0..cnt-1, for x = 0, 1, 2
+template <bool FF>
+__device__ __forceinline__ void dot3(Dot3& d, const dd* a0, const dd* a1, const dd* a2, int as,
+                                     const dd* b0, const dd* b1, const dd* b2, int bs, int cnt) {
+#pragma unroll 1
+  for (int j = 0; j < cnt; ++j) {
+    const int ia = j * as, ib = j * bs;
+    if (FF) {
+      d.c0 = dd_fma_ff(a0[ia].hi, b0[ib].hi, d.c0);
+      d.c1 = dd_fma_ff(a1[ia].hi, b1[ib].hi, d.c1);
+      d.c2 = dd_fma_ff(a2[ia].hi, b2[ib].hi, d.c2);
+    } else {
+      d.c0 = dd_fma(a0[ia], b0[ib], d.c0);
+      d.c1 = dd_fma(a1[ia], b1[ib], d.c1);
+      d.c2 = dd_fma(a2[ia], b2[ib], d.c2);
+    }
+  }
+}
+
 }  // namespace
 
 template <int N>
@@ -77,6 +120,7 @@ __global__ void __launch_bounds__(64) tau_dd_kernel(const int4* __restrict__ tet
                                                     float* __restrict__ eig_out) {
   using L = DDLayout<N>;
   constexpr int NP = L::NP, NM = L::NM, C = L::C, LD = L::LD, NN = L::NN, GPW = L::GPW;
+  constexpr int NT = NM * (NM + 1) / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   dd* smem = reinterpret_cast<dd*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -162,10 +206,10 @@ __global__ void __launch_bounds__(64) tau_dd_kernel(const int4* __restrict__ tet
     __syncwarp();
     // the three convolution matrices C_m = A(w_m) (symmetric)
     if (live)
-      for (int t = k; t < 3 * NN; t += N) {
-        const int m = t / NN, rs = t - m * NN;
-        const int r = rs / NM, s = rs - r * NM;
-        if (r > s) continue;
+      for (int t = k; t < 3 * NT; t += N) {
+        const int m = t / NT;
+        int r, s;
+        tri_rs<NM>(t - m * NT, r, s);
         const dd v = conv_entry_dd<N>(w + m * C, r, s);
         S[m * NN + r * NM + s] = v;
         S[m * NN + s * NM + r] = v;
@@ -173,18 +217,24 @@ __global__ void __launch_bounds__(64) tau_dd_kernel(const int4* __restrict__ tet
     __syncwarp();
     // M = sum_m C_m C_m + C_I nu^2 (G:G) I
     if (live)
-      for (int t = k; t < NN; t += N) {
-        const int r = t / NM, s = t - r * NM;
-        if (r > s) continue;
-        dd acc = (r == s) ? diffd : dd{0.f, 0.f};
+#pragma unroll 1
+      for (int t0 = k; t0 < NT; t0 += 3 * N) {
+        int r[3], c[3];
 #pragma unroll
-        for (int m = 0; m < 3; ++m) {
-          const dd* cr = S + m * NN + r * NM;
-          const dd* cs = S + m * NN + s * NM;
-          for (int j = 0; j < NM; ++j) acc = dd_fma(cr[j], cs[j], acc);
-        }
-        M[r * NM + s] = acc;
-        M[s * NM + r] = acc;
+        for (int x = 0; x < 3; ++x) tri_rs<NM>(t0 + x * N < NT ? t0 + x * N : t0, r[x], c[x]);
+        Dot3 d{r[0] == c[0] ? diffd : dd{0.f, 0.f}, r[1] == c[1] ? diffd : dd{0.f, 0.f},
+               r[2] == c[2] ? diffd : dd{0.f, 0.f}};
+#pragma unroll 1
+        for (int m = 0; m < 3; ++m)
+          dot3<false>(d, S + m * NN + r[0] * NM, S + m * NN + r[1] * NM, S + m * NN + r[2] * NM, 1,
+                      S + m * NN + c[0] * NM, S + m * NN + c[1] * NM, S + m * NN + c[2] * NM, 1, NM);
+        const dd v[3] = {d.c0, d.c1, d.c2};
+#pragma unroll
+        for (int x = 0; x < 3; ++x)
+          if (t0 + x * N < NT) {
+            M[r[x] * NM + c[x]] = v[x];
+            M[c[x] * NM + r[x]] = v[x];
+          }
       }
     __syncwarp();
     // FP32 Jacobi on the leading part (the scratch now holds Mf, Vf)
@@ -206,26 +256,43 @@ __global__ void __launch_bounds__(64) tau_dd_kernel(const int4* __restrict__ tet
 #pragma unroll 1
     for (int it = 0; it < 2; ++it) {
       if (live)
-        for (int t = k; t < NN; t += N) {
-          const int r = t / NM, s = t - r * NM;
-          if (r > s) continue;
-          dd acc = dd{0.f, 0.f};
+#pragma unroll 1
+        for (int t0 = k; t0 < NT; t0 += 3 * N) {
+          int r[3], c[3];
+#pragma unroll
+          for (int x = 0; x < 3; ++x) tri_rs<NM>(t0 + x * N < NT ? t0 + x * N : t0, r[x], c[x]);
+          Dot3 d{dd{0.f, 0.f}, dd{0.f, 0.f}, dd{0.f, 0.f}};
           if (it == 0)
-            for (int i = 0; i < NM; ++i) acc = dd_fma_ff(V[i * NM + r].hi, V[i * NM + s].hi, acc);
+            dot3<true>(d, V + r[0], V + r[1], V + r[2], NM, V + c[0], V + c[1], V + c[2], NM, NM);
           else
-            for (int i = 0; i < NM; ++i) acc = dd_fma(V[i * NM + r], V[i * NM + s], acc);
-          dd h = dd_scale(dd_neg(acc), 0.5f);
-          if (r == s) h = dd_add_f(h, 1.5f);
-          H[r * NM + s] = h;
-          H[s * NM + r] = h;
+            dot3<false>(d, V + r[0], V + r[1], V + r[2], NM, V + c[0], V + c[1], V + c[2], NM, NM);
+          const dd v[3] = {d.c0, d.c1, d.c2};
+#pragma unroll
+          for (int x = 0; x < 3; ++x)
+            if (t0 + x * N < NT) {
+              dd h = dd_scale(dd_neg(v[x]), 0.5f);
+              if (r[x] == c[x]) h = dd_add_f(h, 1.5f);
+              H[r[x] * NM + c[x]] = h;
+              H[c[x] * NM + r[x]] = h;
+            }
         }
       __syncwarp();
       if (live)
-        for (int t = k; t < NN; t += N) {
-          const int r = t / NM, s = t - r * NM;
-          dd acc = dd{0.f, 0.f};
-          for (int j = 0; j < NM; ++j) acc = dd_fma(V[r * NM + j], H[j * NM + s], acc);
-          T[t] = acc;
+#pragma unroll 1
+        for (int t0 = k; t0 < NN; t0 += 3 * N) {
+          int r[3], c[3];
+#pragma unroll
+          for (int x = 0; x < 3; ++x) {
+            const int t = t0 + x * N < NN ? t0 + x * N : t0;
+            r[x] = t / NM;
+            c[x] = t - r[x] * NM;
+          }
+          Dot3 d{dd{0.f, 0.f}, dd{0.f, 0.f}, dd{0.f, 0.f}};
+          dot3<false>(d, V + r[0] * NM, V + r[1] * NM, V + r[2] * NM, 1, H + c[0], H + c[1], H + c[2], NM, NM);
+          const dd v[3] = {d.c0, d.c1, d.c2};
+#pragma unroll
+          for (int x = 0; x < 3; ++x)
+            if (t0 + x * N < NN) T[t0 + x * N] = v[x];
         }
       __syncwarp();
       if (live)
@@ -235,21 +302,38 @@ __global__ void __launch_bounds__(64) tau_dd_kernel(const int4* __restrict__ tet
     // P = M V, B = V^T P (into M)
     dd* P = S;
     if (live)
-      for (int t = k; t < NN; t += N) {
-        const int r = t / NM, s = t - r * NM;
-        dd acc = dd{0.f, 0.f};
-        for (int j = 0; j < NM; ++j) acc = dd_fma(M[r * NM + j], V[j * NM + s], acc);
-        P[t] = acc;
+#pragma unroll 1
+      for (int t0 = k; t0 < NN; t0 += 3 * N) {
+        int r[3], c[3];
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+          const int t = t0 + x * N < NN ? t0 + x * N : t0;
+          r[x] = t / NM;
+          c[x] = t - r[x] * NM;
+        }
+        Dot3 d{dd{0.f, 0.f}, dd{0.f, 0.f}, dd{0.f, 0.f}};
+        dot3<false>(d, M + r[0] * NM, M + r[1] * NM, M + r[2] * NM, 1, V + c[0], V + c[1], V + c[2], NM, NM);
+        const dd v[3] = {d.c0, d.c1, d.c2};
+#pragma unroll
+        for (int x = 0; x < 3; ++x)
+          if (t0 + x * N < NN) P[t0 + x * N] = v[x];
       }
     __syncwarp();
     if (live)
-      for (int t = k; t < NN; t += N) {
-        const int r = t / NM, s = t - r * NM;
-        if (r > s) continue;
-        dd acc = dd{0.f, 0.f};
-        for (int i = 0; i < NM; ++i) acc = dd_fma(V[i * NM + r], P[i * NM + s], acc);
-        M[r * NM + s] = acc;
-        M[s * NM + r] = acc;
+#pragma unroll 1
+      for (int t0 = k; t0 < NT; t0 += 3 * N) {
+        int r[3], c[3];
+#pragma unroll
+        for (int x = 0; x < 3; ++x) tri_rs<NM>(t0 + x * N < NT ? t0 + x * N : t0, r[x], c[x]);
+        Dot3 d{dd{0.f, 0.f}, dd{0.f, 0.f}, dd{0.f, 0.f}};
+        dot3<false>(d, V + r[0], V + r[1], V + r[2], NM, P + c[0], P + c[1], P + c[2], NM, NM);
+        const dd v[3] = {d.c0, d.c1, d.c2};
+#pragma unroll
+        for (int x = 0; x < 3; ++x)
+          if (t0 + x * N < NT) {
+            M[r[x] * NM + c[x]] = v[x];
+            M[c[x] * NM + r[x]] = v[x];
+          }
       }
     __syncwarp();
     // eigenpairs for the derivative of tau (exact tangent), when asked: the
@@ -299,21 +383,37 @@ __global__ void __launch_bounds__(64) tau_dd_kernel(const int4* __restrict__ tet
     __syncwarp();
     // Q = Z V^T, tau = V Q (upper triangle), undo the scale
     if (live)
-      for (int t = k; t < NN; t += N) {
-        const int r = t / NM, s = t - r * NM;
-        dd acc = dd{0.f, 0.f};
-        for (int j = 0; j < NM; ++j) acc = dd_fma(Z[r * NM + j], V[s * NM + j], acc);
-        Q[t] = acc;
+#pragma unroll 1
+      for (int t0 = k; t0 < NN; t0 += 3 * N) {
+        int r[3], c[3];
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+          const int t = t0 + x * N < NN ? t0 + x * N : t0;
+          r[x] = t / NM;
+          c[x] = t - r[x] * NM;
+        }
+        Dot3 d{dd{0.f, 0.f}, dd{0.f, 0.f}, dd{0.f, 0.f}};
+        dot3<false>(d, Z + r[0] * NM, Z + r[1] * NM, Z + r[2] * NM, 1, V + c[0] * NM, V + c[1] * NM,
+                    V + c[2] * NM, 1, NM);
+        const dd v[3] = {d.c0, d.c1, d.c2};
+#pragma unroll
+        for (int x = 0; x < 3; ++x)
+          if (t0 + x * N < NN) Q[t0 + x * N] = v[x];
       }
     __syncwarp();
     if (live) {
       double* out = tau_out + gq * Dims<N>::NT_PAD;
-      for (int t = k; t < NN; t += N) {
-        const int r = t / NM, s = t - r * NM;
-        if (r > s) continue;
-        dd acc = dd{0.f, 0.f};
-        for (int j = 0; j < NM; ++j) acc = dd_fma(V[r * NM + j], Q[j * NM + s], acc);
-        out[packed_index(r, s, NM)] = dd_to_double(acc) * unscale;
+#pragma unroll 1
+      for (int t0 = k; t0 < NT; t0 += 3 * N) {
+        int r[3], c[3];
+#pragma unroll
+        for (int x = 0; x < 3; ++x) tri_rs<NM>(t0 + x * N < NT ? t0 + x * N : t0, r[x], c[x]);
+        Dot3 d{dd{0.f, 0.f}, dd{0.f, 0.f}, dd{0.f, 0.f}};
+        dot3<false>(d, V + r[0] * NM, V + r[1] * NM, V + r[2] * NM, 1, Q + c[0], Q + c[1], Q + c[2], NM, NM);
+        const dd v[3] = {d.c0, d.c1, d.c2};
+#pragma unroll
+        for (int x = 0; x < 3; ++x)
+          if (t0 + x * N < NT) out[t0 + x * N] = dd_to_double(v[x]) * unscale;
       }
       if (k == 0)
         for (int t = Dims<N>::NT; t < Dims<N>::NT_PAD; ++t) out[t] = 0.0;
