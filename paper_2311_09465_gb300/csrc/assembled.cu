@@ -342,13 +342,6 @@ __global__ void __launch_bounds__(256)
   float* buf0 = smem_f + warp * S * L::PWARP;   // [S][HB + NB]
   for (int64_t k = (int64_t)blockIdx.x * wpb + warp; k < n_rows; k += (int64_t)gridDim.x * wpb) {
     const int A = rows[k];
-    // the inverted block of A is read after the connections: ask for it in
-    // L2 now (128-byte lines), so that its product waits on L2, not DRAM
-    {
-      const char* bp = reinterpret_cast<const char*>(binv + (int64_t)A * NB * NB);
-      constexpr int LINES = (NB * NB * 4 + 127) / 128;
-      for (int l = lane; l < LINES; l += 32) asm volatile("prefetch.global.L2 [%0];" ::"l"(bp + 128 * l));
-    }
     float acc[R];
 #pragma unroll
     for (int j = 0; j < R; ++j) acc[j] = 0.f;
@@ -445,22 +438,12 @@ __global__ void __launch_bounds__(256)
     float out[R];
 #pragma unroll
     for (int j = 0; j < R; ++j) out[j] = 0.f;
-    // eight columns per pass: their loads are issued together (NB = 8N)
-#pragma unroll 1
-    for (int col0 = 0; col0 < NB; col0 += 8) {
-      float b[8][R];
+    for (int col = 0; col < NB; ++col) {
+      const float xc = tv[col];
 #pragma unroll
-      for (int u = 0; u < 8; ++u)
-#pragma unroll
-        for (int j = 0; j < R; ++j) {
-          const int o = lane + 32 * j;
-          b[u][j] = o < NB ? Bi[(int64_t)(col0 + u) * NB + o] : 0.f;
-        }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const float xc = tv[col0 + u];
-#pragma unroll
-        for (int j = 0; j < R; ++j) out[j] = fmaf(b[u][j], xc, out[j]);
+      for (int j = 0; j < R; ++j) {
+        const int o = lane + 32 * j;
+        if (o < NB) out[j] = fmaf(Bi[(int64_t)col * NB + o], xc, out[j]);
       }
     }
 #pragma unroll

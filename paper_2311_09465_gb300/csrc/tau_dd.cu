@@ -99,9 +99,10 @@ struct DDLayout {
   static constexpr int NP = 2 * N, NM = 2 * N - 1, C = 2 * N, LD = NP + 1;
   static constexpr int GPW = 32 / N;
   static constexpr int NN = NM * NM;
-  // in 8-byte words (one dd per word).  The scratch holds the three C_m, then
-  // the two FP32 Jacobi matrices, then the refinement's temporaries.
-  static constexpr int SCR = (3 * NN > NP * LD) ? 3 * NN : NP * LD;
+  // in 8-byte words (one dd per word).  The scratch holds one C_m at a time,
+  // then the two FP32 Jacobi matrices, then the refinement's temporaries (at
+  // most two n x n matrices at once).
+  static constexpr int SCR = (2 * NN > NP * LD) ? 2 * NN : NP * LD;
   static constexpr int CM = 0;
   static constexpr int M = CM + SCR;        // [NM][NM] M, later B
   static constexpr int V = M + NN;          // [NM][NM] eigenvectors
@@ -111,7 +112,7 @@ struct DDLayout {
 };
 
 template <int N>
-__global__ void __launch_bounds__(64) tau_dd_kernel(const int4* __restrict__ tets,
+__global__ void __launch_bounds__(128) tau_dd_kernel(const int4* __restrict__ tets,
                                                     const double* __restrict__ geo,
                                                     const double* __restrict__ y, int64_t n_qp,
                                                     double* __restrict__ tau_out, double nu,
@@ -204,39 +205,49 @@ __global__ void __launch_bounds__(64) tau_dd_kernel(const int4* __restrict__ tet
         for (int m = 0; m < 3; ++m) w[m * C + k + h * N] = dd_scale(wl[h][m], sw);
     }
     __syncwarp();
-    // the three convolution matrices C_m = A(w_m) (symmetric)
-    if (live)
-      for (int t = k; t < 3 * NT; t += N) {
-        const int m = t / NT;
-        int r, s;
-        tri_rs<NM>(t - m * NT, r, s);
-        const dd v = conv_entry_dd<N>(w + m * C, r, s);
-        S[m * NN + r * NM + s] = v;
-        S[m * NN + s * NM + r] = v;
-      }
-    __syncwarp();
-    // M = sum_m C_m C_m + C_I nu^2 (G:G) I
-    if (live)
+    // M = sum_m C_m C_m + C_I nu^2 (G:G) I, one convolution matrix C_m = A(w_m)
+    // (symmetric) at a time; M carries the running sum of an entry from one m
+    // to the next exactly (a double-float store), so every entry adds its
+    // terms in the order m = 0, 1, 2, j = 0..n-1
 #pragma unroll 1
-      for (int t0 = k; t0 < NT; t0 += 3 * N) {
-        int r[3], c[3];
-#pragma unroll
-        for (int x = 0; x < 3; ++x) tri_rs<NM>(t0 + x * N < NT ? t0 + x * N : t0, r[x], c[x]);
-        Dot3 d{r[0] == c[0] ? diffd : dd{0.f, 0.f}, r[1] == c[1] ? diffd : dd{0.f, 0.f},
-               r[2] == c[2] ? diffd : dd{0.f, 0.f}};
+    for (int m = 0; m < 3; ++m) {
+      if (live)
+        for (int t = k; t < NT; t += N) {
+          int r, s;
+          tri_rs<NM>(t, r, s);
+          const dd v = conv_entry_dd<N>(w + m * C, r, s);
+          S[r * NM + s] = v;
+          S[s * NM + r] = v;
+        }
+      __syncwarp();
+      if (live)
 #pragma unroll 1
-        for (int m = 0; m < 3; ++m)
-          dot3<false>(d, S + m * NN + r[0] * NM, S + m * NN + r[1] * NM, S + m * NN + r[2] * NM, 1,
-                      S + m * NN + c[0] * NM, S + m * NN + c[1] * NM, S + m * NN + c[2] * NM, 1, NM);
-        const dd v[3] = {d.c0, d.c1, d.c2};
+        for (int t0 = k; t0 < NT; t0 += 3 * N) {
+          int r[3], c[3];
 #pragma unroll
-        for (int x = 0; x < 3; ++x)
-          if (t0 + x * N < NT) {
-            M[r[x] * NM + c[x]] = v[x];
-            M[c[x] * NM + r[x]] = v[x];
+          for (int x = 0; x < 3; ++x) tri_rs<NM>(t0 + x * N < NT ? t0 + x * N : t0, r[x], c[x]);
+          Dot3 d;
+          if (m == 0) {
+            d.c0 = r[0] == c[0] ? diffd : dd{0.f, 0.f};
+            d.c1 = r[1] == c[1] ? diffd : dd{0.f, 0.f};
+            d.c2 = r[2] == c[2] ? diffd : dd{0.f, 0.f};
+          } else {
+            d.c0 = M[r[0] * NM + c[0]];
+            d.c1 = M[r[1] * NM + c[1]];
+            d.c2 = M[r[2] * NM + c[2]];
           }
-      }
-    __syncwarp();
+          dot3<false>(d, S + r[0] * NM, S + r[1] * NM, S + r[2] * NM, 1, S + c[0] * NM, S + c[1] * NM,
+                      S + c[2] * NM, 1, NM);
+          const dd v[3] = {d.c0, d.c1, d.c2};
+#pragma unroll
+          for (int x = 0; x < 3; ++x)
+            if (t0 + x * N < NT) {
+              M[r[x] * NM + c[x]] = v[x];
+              M[c[x] * NM + r[x]] = v[x];
+            }
+        }
+      __syncwarp();
+    }
     // FP32 Jacobi on the leading part (the scratch now holds Mf, Vf)
     if (live)
       for (int t = k; t < NP * NP; t += N) {
@@ -362,7 +373,7 @@ __global__ void __launch_bounds__(64) tau_dd_kernel(const int4* __restrict__ tet
     // X_ik = E_ik / (s_i s_k (s_i + s_k)) in FP32 (first order in E)
     float* X = reinterpret_cast<float*>(S);
     dd* Z = S + NN;
-    dd* Q = S + 2 * NN;
+    dd* Q = S;   // over X, which only the Z phase reads
     if (live)
       for (int t = k; t < NN; t += N) {
         const int r = t / NM, s = t - r * NM;
@@ -427,7 +438,18 @@ int launch_tau_dd(const int4* tets, const double* geo, const double* y, int64_t 
                   double* tau_out, double nu, double C_I, unsigned* n_unconverged,
                   cudaStream_t st, float* eig_out) {
   using L = DDLayout<N>;
-  const int warps = ((size_t)2 * L::WARP * sizeof(dd) <= 100 * 1024) ? 2 : 1;
+  // warps per block (1..4) that keep the most warps resident per SM: the
+  // shared footprint is the limit (228 KB per SM, 1 KB of it reserved per block)
+  int warps = 1, best = 0;
+  for (int wb = 1; wb <= 4; ++wb) {
+    const size_t per_block = (size_t)wb * L::WARP * sizeof(dd);
+    if (per_block > 227 * 1024) break;
+    const int resident = wb * (int)((228 * 1024) / (per_block + 1024));
+    if (resident > best) {
+      best = resident;
+      warps = wb;
+    }
+  }
   const size_t smem = (size_t)warps * L::WARP * sizeof(dd);
   if (smem > 227 * 1024) return -6;
   cudaFuncSetAttribute(tau_dd_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
