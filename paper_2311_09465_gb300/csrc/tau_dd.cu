@@ -107,7 +107,11 @@ struct DDLayout {
   static constexpr int M = CM + SCR;        // [NM][NM] M, later B
   static constexpr int V = M + NN;          // [NM][NM] eigenvectors
   static constexpr int W = V + NN;          // [3][C] w_m, later sqrt(b_ii), 1/sqrt(b_ii), floats
-  static constexpr int GROUP = W + 3 * C;
+  // a point's block, padded to N (mod 16) words of 8 bytes: the N lanes of a
+  // group read N consecutive words of a row, and consecutive groups then
+  // start 2N banks apart, so the groups of a warp do not share banks
+  static constexpr int GROUP_RAW = W + 3 * C;
+  static constexpr int GROUP = GROUP_RAW + ((N - GROUP_RAW) % 16 + 16) % 16;
   static constexpr int WARP = GROUP * GPW + 32;   // + 64 floats of reduction scratch
 };
 
