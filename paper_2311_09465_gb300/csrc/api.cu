@@ -130,7 +130,6 @@ struct ts_problem {
   double *d_w = nullptr, *d_r = nullptr, *d_dy = nullptr, *d_partial = nullptr, *d_h = nullptr;
   float *d_v32 = nullptr, *d_w32 = nullptr;
   double *d_D = nullptr, *d_t = nullptr;      // preconditioner diagonal (inverted), temp
-  double* d_vk = nullptr;                     // a double-float basis vector in FP64 (mixed solve)
   float* d_binv = nullptr;                    // inverted nodal blocks [V][8N][8N] (block Jacobi)
   bool binv_valid = false;                    // d_binv built at the current linearisation state
   float* d_eig = nullptr;                     // eigenpairs of M per point [E*4][EIG] (exact tangent)
@@ -674,17 +673,21 @@ static int spmv_any(ts_problem* pr, const float* v, float* hv, cudaStream_t st) 
 }
 
 // Symmetric block Gauss-Seidel with the assembled records (precond 3): a
-// forward sweep over the node colours from z = 0, then a backward sweep
+// forward sweep over the node colours from z = 0, then a backward sweep.
+// Two updates are left out because their result is known exactly: the first
+// colour of the forward sweep sees z = 0 everywhere else (its off-diagonal
+// sum is zero: z_A = Binv_A r_A), and the first colour of the backward sweep
+// is the forward sweep's last, whose neighbours have not changed since.
 template <int N>
 static int sgs_impl(ts_problem* pr, cudaStream_t st) {
   const ts_mesh* m = pr->mesh;
   const int nc = (int)m->ncolour_off.size() - 1;
   for (int pass = 0; pass < 2; ++pass)
-    for (int k = 0; k < nc; ++k) {
+    for (int k = pass; k < nc; ++k) {
       const int c = pass == 0 ? k : nc - 1 - k;
       const int64_t o0 = m->ncolour_off[c], o1 = m->ncolour_off[c + 1];
       if (launch_sgs_colour<N>(m->d_node_perm + o0, o1 - o0, m->d_row_off, m->d_cols, pr->d_hasm, pr->d_binv,
-                               pr->d_dmask, pr->d_r32, pr->d_z32, st))
+                               pr->d_dmask, pr->d_r32, pr->d_z32, pass == 0 && k == 0, st))
         return fail(TS_ERR_CUDA, "block Gauss-Seidel kernel launch failed");
     }
   return 0;
@@ -1060,7 +1063,6 @@ void ts_problem_free(ts_problem* pr) {
   dfree(pr->d_w32);
   dfree(pr->d_D);
   dfree(pr->d_t);
-  dfree(pr->d_vk);
   dfree(pr->d_binv);
   dfree(pr->d_eig);
   dfree(pr->d_dT);
@@ -1916,18 +1918,10 @@ int ts_solve(ts_problem* pr, void* y_inout, const ts_solve_opts* opts, ts_solve_
     TS_TRY(dalloc(&pr->d_w32, n));
     TS_TRY(dalloc(&pr->d_D, n));
     TS_TRY(dalloc(&pr->d_t, n));
-    TS_TRY(dalloc(&pr->d_vk, n));
   }
   if (o.krylov > 128) return fail(TS_ERR_ARG, "ts_solve: krylov must be <= 128");
   double* y = (double*)y_inout;
   double* V = pr->d_basis;
-  // the mixed-precision solve keeps its basis as double-float pairs in the
-  // same storage (8 bytes per entry) and orthogonalises on the FP32 pipe;
-  // the w_dd scratch of its dots is the preconditioner's temporary, free
-  // between the product and the next preconditioner application
-  const bool ddk = o.precision == 32;
-  float2* Vd = reinterpret_cast<float2*>(pr->d_basis);
-  float2* w_dd = reinterpret_cast<float2*>(pr->d_t);
   const double t_start = now_s();
   std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), yk(m);
   double r_ref = o.r_ref;
@@ -2009,8 +2003,7 @@ int ts_solve(ts_problem* pr, void* y_inout, const ts_solve_opts* opts, ts_solve_
     double lin_res = bnorm;   // last estimate of the linear residual
     while (!done && nmv < o.max_matvec) {
       // V0 = -(current linear residual) / beta ; the residual lives in d_w
-      if (ddk ? vec_split_scale(Vd, pr->d_w, -1.0 / beta, n, st) : vec_scale(V, pr->d_w, -1.0 / beta, n, st))
-        return fail(TS_ERR_CUDA, "scale");
+      if (vec_scale(V, pr->d_w, -1.0 / beta, n, st)) return fail(TS_ERR_CUDA, "scale");
       std::fill(g.begin(), g.end(), 0.0);
       g[0] = beta;
       int k_used = 0;
@@ -2018,10 +2011,6 @@ int ts_solve(ts_problem* pr, void* y_inout, const ts_solve_opts* opts, ts_solve_
         const double tj = now_s();
         TS_CUDA(cudaEventRecord(pr->ev_a, st));
         double* vk = V + (int64_t)k * n;
-        if (ddk) {
-          if (vec_join(pr->d_vk, Vd + (int64_t)k * n, n, st)) return fail(TS_ERR_CUDA, "join");
-          vk = pr->d_vk;
-        }
         if (o.precond == 1) {
           if (vec_mul(pr->d_t, pr->d_D, vk, n, st)) return fail(TS_ERR_CUDA, "mul");
           vk = pr->d_t;
@@ -2049,26 +2038,13 @@ int ts_solve(ts_problem* pr, void* y_inout, const ts_solve_opts* opts, ts_solve_
         double* dh2 = pr->d_h + 130;
         double* dn2 = pr->d_h + 260;
         double* dskip = pr->d_h + 390;
-        if (ddk) {
-          if (krylov_dots_dd(Vd, n, k + 1, pr->d_w, w_dd, n, pr->d_partial, dh1, st, 1))
-            return fail(TS_ERR_CUDA, "dots");
-          if (krylov_sub_dd(pr->d_w, Vd, n, k + 1, dh1, n, st)) return fail(TS_ERR_CUDA, "sub");
-          if (krylov_reorth_test(dh1, k + 1, dskip, st)) return fail(TS_ERR_CUDA, "reorth test");
-          if (krylov_dots_dd(Vd, n, k + 1, pr->d_w, w_dd, n, pr->d_partial, dh2, st, 0, dskip))
-            return fail(TS_ERR_CUDA, "dots");
-          if (krylov_sub_dd(pr->d_w, Vd, n, k + 1, dh2, n, st, dskip)) return fail(TS_ERR_CUDA, "sub");
-          if (krylov_dots(pr->d_w, n, 1, pr->d_w, n, pr->d_partial, dn2, st)) return fail(TS_ERR_CUDA, "norm");
-          if (vec_split_normalise(Vd + (int64_t)(k + 1) * n, pr->d_w, dn2, n, st))
-            return fail(TS_ERR_CUDA, "normalise");
-        } else {
-          if (krylov_dots(V, n, k + 1, pr->d_w, n, pr->d_partial, dh1, st, 1)) return fail(TS_ERR_CUDA, "dots");
-          if (krylov_sub(pr->d_w, V, n, k + 1, dh1, n, st)) return fail(TS_ERR_CUDA, "sub");
-          if (krylov_reorth_test(dh1, k + 1, dskip, st)) return fail(TS_ERR_CUDA, "reorth test");
-          if (krylov_dots(V, n, k + 1, pr->d_w, n, pr->d_partial, dh2, st, 0, dskip)) return fail(TS_ERR_CUDA, "dots");
-          if (krylov_sub(pr->d_w, V, n, k + 1, dh2, n, st, dskip)) return fail(TS_ERR_CUDA, "sub");
-          if (krylov_dots(pr->d_w, n, 1, pr->d_w, n, pr->d_partial, dn2, st)) return fail(TS_ERR_CUDA, "norm");
-          if (vec_normalise(V + (int64_t)(k + 1) * n, pr->d_w, dn2, n, st)) return fail(TS_ERR_CUDA, "normalise");
-        }
+        if (krylov_dots(V, n, k + 1, pr->d_w, n, pr->d_partial, dh1, st, 1)) return fail(TS_ERR_CUDA, "dots");
+        if (krylov_sub(pr->d_w, V, n, k + 1, dh1, n, st)) return fail(TS_ERR_CUDA, "sub");
+        if (krylov_reorth_test(dh1, k + 1, dskip, st)) return fail(TS_ERR_CUDA, "reorth test");
+        if (krylov_dots(V, n, k + 1, pr->d_w, n, pr->d_partial, dh2, st, 0, dskip)) return fail(TS_ERR_CUDA, "dots");
+        if (krylov_sub(pr->d_w, V, n, k + 1, dh2, n, st, dskip)) return fail(TS_ERR_CUDA, "sub");
+        if (krylov_dots(pr->d_w, n, 1, pr->d_w, n, pr->d_partial, dn2, st)) return fail(TS_ERR_CUDA, "norm");
+        if (vec_normalise(V + (int64_t)(k + 1) * n, pr->d_w, dn2, n, st)) return fail(TS_ERR_CUDA, "normalise");
         double hh[3 * 130];
         TS_CUDA(cudaMemcpyAsync(hh, pr->d_h, 3 * 130 * sizeof(double), cudaMemcpyDeviceToHost, st));
         TS_CUDA(cudaStreamSynchronize(st));
@@ -2106,9 +2082,7 @@ int ts_solve(ts_problem* pr, void* y_inout, const ts_solve_opts* opts, ts_solve_
       }
       double tk = now_s();
       TS_CUDA(cudaMemcpyAsync(pr->d_h, yk.data(), k_used * sizeof(double), cudaMemcpyHostToDevice, st));
-      if (ddk ? krylov_combine_dd(pr->d_w, Vd, n, k_used, pr->d_h, n, st)
-              : krylov_combine(pr->d_w, V, n, k_used, pr->d_h, n, st))
-        return fail(TS_ERR_CUDA, "combine");
+      if (krylov_combine(pr->d_w, V, n, k_used, pr->d_h, n, st)) return fail(TS_ERR_CUDA, "combine");
       const double* upd = pr->d_w;
       if (o.precond == 1 && vec_mul(pr->d_w, pr->d_D, pr->d_w, n, st)) return fail(TS_ERR_CUDA, "mul");
       if (o.precond == 2) {

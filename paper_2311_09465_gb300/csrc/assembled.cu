@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(256)
     sgs_colour_kernel(const int32_t* __restrict__ rows, int64_t n_rows, const int32_t* __restrict__ row_off,
                       const int32_t* __restrict__ cols, const float* __restrict__ H,
                       const float* __restrict__ binv, const uint8_t* __restrict__ dmask,
-                      const float* __restrict__ r, float* __restrict__ z) {
+                      const float* __restrict__ r, float* __restrict__ z, int diag_only) {
   using L = AsmLayout<N>;
   constexpr int C = L::C, CC = L::CC, HB = L::HB, NB = 4 * C, S = SGS_STAGES;
   constexpr int R = (NB + 31) / 32;
@@ -357,7 +357,8 @@ __global__ void __launch_bounds__(256)
         break;
       }
     }
-    const int n_off = (r1 - r0) - (pd < r1 ? 1 : 0);
+    // diag_only: every z_B is zero (the sweep's first colour), so is the sum
+    const int n_off = diag_only ? 0 : (r1 - r0) - (pd < r1 ? 1 : 0);
     auto conn = [&](int i) { return r0 + i + (r0 + i >= pd ? 1 : 0); };
     // one commit group per ring position, empty past the row's end, so that
     // waiting for all but the newest S - 1 groups always means "slot i landed"
@@ -458,7 +459,7 @@ __global__ void __launch_bounds__(256)
 template <int N>
 int launch_sgs_colour(const int32_t* rows, int64_t n_rows, const int32_t* row_off, const int32_t* cols,
                       const float* H, const float* binv, const uint8_t* dmask, const float* r, float* z,
-                      cudaStream_t st) {
+                      int diag_only, cudaStream_t st) {
   using L = AsmLayout<N>;
   if (n_rows <= 0) return 0;
   int warps = 8;
@@ -469,7 +470,8 @@ int launch_sgs_colour(const int32_t* rows, int64_t n_rows, const int32_t* row_of
   int64_t blocks = (n_rows + warps - 1) / warps;
   if (blocks > 152 * 64) blocks = 152 * 64;
   count_launches(1);
-  sgs_colour_kernel<N><<<(int)blocks, warps * 32, smem, st>>>(rows, n_rows, row_off, cols, H, binv, dmask, r, z);
+  sgs_colour_kernel<N><<<(int)blocks, warps * 32, smem, st>>>(rows, n_rows, row_off, cols, H, binv, dmask, r, z,
+                                                               diag_only);
   return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
@@ -518,7 +520,7 @@ TS_FOR_EACH_N(TS_INST_ASM, float)
 TS_FOR_EACH_N(TS_INST_ASM, double)
 #define TS_INST_SGS(T, N)                                                                                  \
   template int launch_sgs_colour<N>(const int32_t*, int64_t, const int32_t*, const int32_t*, const float*, \
-                                    const float*, const uint8_t*, const float*, float*, cudaStream_t);
+                                    const float*, const uint8_t*, const float*, float*, int, cudaStream_t);
 TS_FOR_EACH_N(TS_INST_SGS, float)
 #define TS_INST_SPMV(T, N)                                                                          \
   template int launch_spmv_paper<N>(const int32_t*, const int32_t*, const float*, const uint8_t*, \

@@ -165,7 +165,7 @@ int assembled_record_floats(int N);
 template <int N>
 int launch_sgs_colour(const int32_t* rows, int64_t n_rows, const int32_t* row_off, const int32_t* cols,
                       const float* H, const float* binv, const uint8_t* dmask, const float* r, float* z,
-                      cudaStream_t st);
+                      int diag_only, cudaStream_t st);
 
 // FP64 Krylov helpers (krylov.cu)
 // h_out[j] = basis_j . w (j < nvec), with self also h_out[nvec] = w . w;
@@ -185,20 +185,6 @@ int vec_axpy(double* y, const double* x, double a, int64_t n, cudaStream_t st);
 int vec_cast_d2f(float* out, const double* in, int64_t n, cudaStream_t st);
 int vec_cast_f2d(double* out, const float* in, int64_t n, cudaStream_t st);
 int krylov_partial_blocks();
-// The same operations with the basis held as double-float pairs (float2 hi,
-// lo; the mixed-precision solve): dots split w into w_dd (n pairs of scratch)
-// first; sub and combine accumulate in double-float and write FP64
-int krylov_dots_dd(const float2* basis, int64_t ld, int nvec, const double* w, float2* w_dd, int64_t n,
-                   double* partial, double* h_out, cudaStream_t st, int self = 0,
-                   const double* skip = nullptr);
-int krylov_sub_dd(double* w, const float2* basis, int64_t ld, int nvec, const double* h, int64_t n,
-                  cudaStream_t st, const double* skip = nullptr);
-int krylov_combine_dd(double* x, const float2* basis, int64_t ld, int nvec, const double* coef, int64_t n,
-                      cudaStream_t st);
-// out = split(a in); out = split(in / sqrt(*n2)); out = hi + lo
-int vec_split_scale(float2* out, const double* in, double a, int64_t n, cudaStream_t st);
-int vec_split_normalise(float2* out, const double* in, const double* n2, int64_t n, cudaStream_t st);
-int vec_join(double* out, const float2* in, int64_t n, cudaStream_t st);
 int vec_mul(double* out, const double* a, const double* b, int64_t n, cudaStream_t st);
 // out = in / sqrt(*n2) with the squared norm read on the device
 int vec_normalise(double* out, const double* in, const double* n2, int64_t n, cudaStream_t st);

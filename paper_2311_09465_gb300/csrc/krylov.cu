@@ -6,7 +6,6 @@
 // Reductions are two-stage and deterministic: a fixed grid of blocks writes
 // per-block partial sums, one warp per vector adds them in block order.
 #include "common.cuh"
-#include "ddfloat.cuh"
 #include "kernels.h"
 
 namespace ts {
@@ -186,184 +185,6 @@ __global__ void combine_kernel(double* __restrict__ x, const double* __restrict_
     for (int j = 0; j < nvec; ++j) acc += sh[j] * basis[(int64_t)j * ld + i];
     x[i] = acc;
   }
-}
-
-// ------------------------------------------------- double-float Krylov basis
-// The mixed-precision solve keeps its Krylov basis as double-float pairs
-// (hi, lo) of FP32 numbers, 8 bytes per entry like FP64, and runs the
-// Gram-Schmidt multiply-adds on the FP32 pipe (ddfloat.cuh; GB300 issues
-// FP32 at 64 times its FP64 rate, so the FP64 dots were bound by the FP64
-// pipe, not by HBM).  The vector being orthogonalised, the coefficients and
-// the reductions across blocks stay FP64.  A double-float sum carries an
-// absolute error near 2^-46 of its largest term, far below the FP32 tangent
-// products that feed this basis.
-
-__device__ __forceinline__ float2 dd_split(double x) {
-  const float h = (float)x;
-  return make_float2(h, (float)(x - (double)h));
-}
-__device__ __forceinline__ dd dd_of(float2 v) { return dd{v.x, v.y}; }
-__device__ __forceinline__ double dd_join(dd a) { return (double)a.hi + (double)a.lo; }
-
-// out = split(a * in)
-__global__ void split_scale_kernel(float2* __restrict__ out, const double* __restrict__ in, double a, int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = dd_split(a * in[i]);
-}
-
-// out = split(in / sqrt(*n2)) (zero when the norm vanishes)
-__global__ void split_normalise_kernel(float2* __restrict__ out, const double* __restrict__ in,
-                                       const double* __restrict__ n2, int64_t n) {
-  const double v = *n2;
-  const double sc = v > 0 ? 1.0 / sqrt(v) : 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = dd_split(in[i] * sc);
-}
-
-// out = hi + lo in FP64
-__global__ void join_kernel(double* __restrict__ out, const float2* __restrict__ in, int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = dd_join(dd_of(in[i]));
-}
-
-// partial[j * gridDim.x + b] = block b's part of basis_j . w, j < nvec (the
-// same blocking as dots_kernel), and with self != 0 row nvec = w . w; w given
-// as double-float pairs
-__global__ void __launch_bounds__(RED_THREADS) dots_dd_kernel(const float2* __restrict__ basis, int64_t ld,
-                                                              int nvec, const float2* __restrict__ w,
-                                                              int64_t n, double* __restrict__ partial, int self,
-                                                              const double* __restrict__ skip) {
-  const int nout = nvec + (self ? 1 : 0);
-  if (skip != nullptr && *skip != 0.0) {
-    for (int j = threadIdx.x; j < nout; j += blockDim.x) partial[(int64_t)j * gridDim.x + blockIdx.x] = 0.0;
-    return;
-  }
-  __shared__ double red[RED_THREADS / 32][4];
-  const int64_t chunk = ((n + gridDim.x - 1) / gridDim.x + 1) & ~(int64_t)1;
-  const int64_t i0 = (int64_t)blockIdx.x * chunk;
-  const int64_t i1 = i0 + chunk < n ? i0 + chunk : n;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  dd self_acc{0.f, 0.f};
-  for (int j0 = 0; j0 < nvec; j0 += 4) {
-    const int nj = nvec - j0 < 4 ? nvec - j0 : 4;
-    dd acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-    const bool with_self = self && j0 == 0;
-    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-      const dd wi = dd_of(w[i]);
-#pragma unroll
-      for (int jj = 0; jj < 4; ++jj)
-        if (jj < nj) acc[jj] = dd_fma(dd_of(basis[(int64_t)(j0 + jj) * ld + i]), wi, acc[jj]);
-      if (with_self) self_acc = dd_fma(wi, wi, self_acc);
-    }
-#pragma unroll
-    for (int jj = 0; jj < 4; ++jj) {
-      const double sum = warp_sum(dd_join(acc[jj]));
-      if (lane == 0) red[warp][jj] = sum;
-    }
-    __syncthreads();
-    if ((int)threadIdx.x < nj) {
-      double t = 0;
-      for (int k = 0; k < RED_THREADS / 32; ++k) t += red[k][threadIdx.x];
-      partial[(int64_t)(j0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
-    }
-    __syncthreads();
-  }
-  if (self) {
-    const double sum = warp_sum(dd_join(self_acc));
-    if (lane == 0) red[warp][0] = sum;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0;
-      for (int k = 0; k < RED_THREADS / 32; ++k) t += red[k][0];
-      partial[(int64_t)nvec * gridDim.x + blockIdx.x] = t;
-    }
-  }
-}
-
-// w -= sum_j h_j basis_j with the sum in double-float (nothing when *skip != 0)
-__global__ void sub_dd_kernel(double* __restrict__ w, const float2* __restrict__ basis, int64_t ld, int nvec,
-                              const double* __restrict__ h, int64_t n, const double* __restrict__ skip) {
-  if (skip != nullptr && *skip != 0.0) return;
-  extern __shared__ float2 shh[];
-  for (int j = threadIdx.x; j < nvec; j += blockDim.x) shh[j] = dd_split(-h[j]);
-  __syncthreads();
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const float2 w0 = dd_split(w[i]);
-    dd acc = dd_of(w0);
-    int j = 0;
-    for (; j + 3 < nvec; j += 4) {
-      float2 b[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) b[u] = basis[(int64_t)(j + u) * ld + i];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) acc = dd_fma(dd_of(shh[j + u]), dd_of(b[u]), acc);
-    }
-    for (; j < nvec; ++j) acc = dd_fma(dd_of(shh[j]), dd_of(basis[(int64_t)j * ld + i]), acc);
-    w[i] = dd_join(acc);
-  }
-}
-
-// x = sum_j c_j basis_j with the sum in double-float
-__global__ void combine_dd_kernel(double* __restrict__ x, const float2* __restrict__ basis, int64_t ld, int nvec,
-                                  const double* __restrict__ c, int64_t n) {
-  extern __shared__ float2 shc[];
-  for (int j = threadIdx.x; j < nvec; j += blockDim.x) shc[j] = dd_split(c[j]);
-  __syncthreads();
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    dd acc{0.f, 0.f};
-    for (int j = 0; j < nvec; ++j) acc = dd_fma(dd_of(shc[j]), dd_of(basis[(int64_t)j * ld + i]), acc);
-    x[i] = dd_join(acc);
-  }
-}
-
-// w as double-float pairs (the operand of dots_dd_kernel)
-__global__ void split_kernel(float2* __restrict__ out, const double* __restrict__ in, int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = dd_split(in[i]);
-}
-
-static int grid_for(int64_t n);
-
-int krylov_dots_dd(const float2* basis, int64_t ld, int nvec, const double* w, float2* w_dd, int64_t n,
-                   double* partial, double* h_out, cudaStream_t st, int self, const double* skip) {
-  const int nout = nvec + (self ? 1 : 0);
-  count_launches(3);
-  split_kernel<<<grid_for(n), 256, 0, st>>>(w_dd, w, n);
-  dots_dd_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(basis, ld, nvec, w_dd, n, partial, self, skip);
-  sum_partials_kernel<<<(nout + 3) / 4, 128, 0, st>>>(partial, RED_BLOCKS, nout, h_out);
-  return cudaGetLastError() == cudaSuccess ? 0 : -2;
-}
-
-int krylov_sub_dd(double* w, const float2* basis, int64_t ld, int nvec, const double* h, int64_t n,
-                  cudaStream_t st, const double* skip) {
-  count_launches(1);
-  sub_dd_kernel<<<grid_for(n), 256, nvec * sizeof(float2), st>>>(w, basis, ld, nvec, h, n, skip);
-  return cudaGetLastError() == cudaSuccess ? 0 : -2;
-}
-
-int krylov_combine_dd(double* x, const float2* basis, int64_t ld, int nvec, const double* coef, int64_t n,
-                      cudaStream_t st) {
-  count_launches(1);
-  combine_dd_kernel<<<grid_for(n), 256, nvec * sizeof(float2), st>>>(x, basis, ld, nvec, coef, n);
-  return cudaGetLastError() == cudaSuccess ? 0 : -2;
-}
-
-int vec_split_scale(float2* out, const double* in, double a, int64_t n, cudaStream_t st) {
-  count_launches(1);
-  split_scale_kernel<<<grid_for(n), 256, 0, st>>>(out, in, a, n);
-  return cudaGetLastError() == cudaSuccess ? 0 : -2;
-}
-
-int vec_split_normalise(float2* out, const double* in, const double* n2, int64_t n, cudaStream_t st) {
-  count_launches(1);
-  split_normalise_kernel<<<grid_for(n), 256, 0, st>>>(out, in, n2, n);
-  return cudaGetLastError() == cudaSuccess ? 0 : -2;
-}
-
-int vec_join(double* out, const float2* in, int64_t n, cudaStream_t st) {
-  count_launches(1);
-  join_kernel<<<grid_for(n), 256, 0, st>>>(out, in, n);
-  return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
 static int grid_for(int64_t n) {
