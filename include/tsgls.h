@@ -77,6 +77,16 @@ extern "C" {
 #define TS_ELEMENT64_NATIVE 0  /*   FP64 instructions                                     */
 #define TS_ELEMENT64_DOUBLEFLOAT 1 /* double-float pairs on the FP32 pipe (FP64 storage;  */
                                    /* default): meets the FP64 bar, 1.5x faster           */
+#define TS_OPT_TAU_WARM     4  /* 0 (default): every FP64 residual with TS_TAU64_DOUBLEFLOAT */
+                               /* computes tau from scratch; 1: its FP32 Jacobi sweeps     */
+                               /* start from each quadrature point's eigenvectors of the   */
+                               /* previous evaluation on this problem (cached, (2N-1)^2    */
+                               /* floats per point, allocated on first use), so they stop  */
+                               /* early when the state moved little.  The refinement makes */
+                               /* tau independent of the start up to rounding (about 1e-15 */
+                               /* relative), not bitwise.  Setting the key drops the cache; */
+                               /* ts_solve uses 1 for its own residuals and restores the   */
+                               /* caller's value on return.                                */
 
 typedef struct ts_mesh ts_mesh;
 typedef struct ts_problem ts_problem;
@@ -139,7 +149,10 @@ typedef struct {
   int    hist_len;      /* entries written to hist                              */
   double hist[512];     /* ||r||/r_ref after each step (rejected ones included) */
   int    rejected;      /* steps undone by the reject test                      */
-  double t_precond;     /* seconds building the preconditioner (precond 1 or 2) */
+  double t_precond;     /* seconds building the preconditioner (precond 1, 2, 3) */
+  double t_tau;         /* seconds in the tau launches of the residuals (CUDA   */
+                        /* events around each launch on the solve's stream)     */
+  int    n_residual;    /* residual evaluations (each one tau launch)           */
 } ts_solve_report;
 
 /* Copies a tetrahedral mesh to the device and precomputes per-element shape

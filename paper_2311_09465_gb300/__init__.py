@@ -25,7 +25,7 @@ TS_PROFILE_PARABOLIC, TS_PROFILE_WOMERSLEY = 1, 2
 PROFILES = {"parabolic": TS_PROFILE_PARABOLIC, "womersley": TS_PROFILE_WOMERSLEY}
 TS_JVP_PAPER, TS_JVP_FROZEN, TS_JVP_LIN_A, TS_JVP_EXACT = 0, 1, 2, 3
 VARIANTS = {"paper": TS_JVP_PAPER, "frozen": TS_JVP_FROZEN, "lin_a": TS_JVP_LIN_A, "exact": TS_JVP_EXACT}
-TS_OPT_TAU64, TS_OPT_FP32_TANGENT, TS_OPT_ELEMENT64 = 1, 2, 3
+TS_OPT_TAU64, TS_OPT_FP32_TANGENT, TS_OPT_ELEMENT64, TS_OPT_TAU_WARM = 1, 2, 3, 4
 ELEMENT64 = {"native": 0, "doublefloat": 1}
 TS_TAU64_REFINE, TS_TAU64_DOUBLEFLOAT, TS_TAU64_JACOBI = 0, 1, 2
 TAU64 = {"refine": TS_TAU64_REFINE, "doublefloat": TS_TAU64_DOUBLEFLOAT, "jacobi": TS_TAU64_JACOBI}
@@ -57,7 +57,8 @@ class ts_solve_report(ctypes.Structure):
                 ("t_residual", ctypes.c_double), ("t_jvp", ctypes.c_double),
                 ("t_krylov", ctypes.c_double), ("hist_len", ctypes.c_int),
                 ("hist", ctypes.c_double * 512), ("rejected", ctypes.c_int),
-                ("t_precond", ctypes.c_double)]
+                ("t_precond", ctypes.c_double), ("t_tau", ctypes.c_double),
+                ("n_residual", ctypes.c_int)]
 
     def to_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k != "hist"}
@@ -389,9 +390,11 @@ class GLSProblem:
             ts_set_bc(self.prob, tag, TS_BC_BACKFLOW, beta)
         self.option(tau64=tau64, fp32_tangent=fp32_tangent, element64=element64)
 
-    def option(self, tau64=None, fp32_tangent=None, element64=None):
+    def option(self, tau64=None, fp32_tangent=None, element64=None, tau_warm=None):
         """tau64: "refine" | "doublefloat" | "jacobi"; fp32_tangent: "single" | "coloured";
-        element64: "native" | "doublefloat"."""
+        element64: "native" | "doublefloat"; tau_warm: bool (warm-started tau eigensolve)."""
+        if tau_warm is not None:
+            ts_problem_option(self.prob, TS_OPT_TAU_WARM, int(bool(tau_warm)))
         if element64 is not None:
             ts_problem_option(self.prob, TS_OPT_ELEMENT64, ELEMENT64[element64])
         if tau64 is not None:

@@ -131,6 +131,9 @@ struct ts_problem {
   float *d_v32 = nullptr, *d_w32 = nullptr;
   double *d_D = nullptr, *d_t = nullptr;      // preconditioner diagonal (inverted), temp
   float* d_binv = nullptr;                    // inverted nodal blocks [V][8N][8N] (block Jacobi)
+  int tau_warm = 0;                           // TS_OPT_TAU_WARM
+  float* d_vcache = nullptr;                  // eigenvectors of M per point [E*4][(2N-1)^2] (warm start)
+  bool vcache_valid = false;
   bool binv_valid = false;                    // d_binv built at the current linearisation state
   float* d_eig = nullptr;                     // eigenpairs of M per point [E*4][EIG] (exact tangent)
   float* d_dT = nullptr;                      // d tau[v] L(u0) per point [E][4][3][C] (exact tangent)
@@ -371,9 +374,18 @@ static int residual_impl(ts_problem* pr, const T* y, T* r, cudaStream_t st) {
     if (pr->tau64 == TS_TAU64_JACOBI)
       rc = launch_tau<T, N>(m->d_tets, geo_of<T>(m), y, m->E, l.tau, (T)(pr->p.mu / pr->p.rho),
                             (T)pr->p.C_I, pr->d_counter, st, eig);
-    else if (pr->tau64 == TS_TAU64_DOUBLEFLOAT)
+    else if (pr->tau64 == TS_TAU64_DOUBLEFLOAT) {
+      float* vc = nullptr;
+      if (pr->tau_warm) {
+        constexpr int64_t NMN = (2 * N - 1) * (2 * N - 1);
+        if (!pr->d_vcache) TS_TRY(dalloc(&pr->d_vcache, (size_t)(m->E * 4 * NMN)));
+        vc = pr->d_vcache;
+      }
       rc = launch_tau_dd<N>(m->d_tets, m->d_geo64, (const double*)y, m->E, (double*)l.tau,
-                            pr->p.mu / pr->p.rho, pr->p.C_I, pr->d_counter, st, eig);
+                            pr->p.mu / pr->p.rho, pr->p.C_I, pr->d_counter, st, eig, vc,
+                            pr->vcache_valid ? 1 : 0);
+      if (vc && rc == 0) pr->vcache_valid = true;
+    }
     else
       rc = launch_tau_polish<N>(m->d_tets, m->d_geo64, (const double*)y, m->E, (double*)l.tau,
                                 pr->p.mu / pr->p.rho, pr->p.C_I, pr->d_counter, st, eig);
@@ -1064,6 +1076,7 @@ void ts_problem_free(ts_problem* pr) {
   dfree(pr->d_D);
   dfree(pr->d_t);
   dfree(pr->d_binv);
+  dfree(pr->d_vcache);
   dfree(pr->d_eig);
   dfree(pr->d_dT);
   dfree(pr->d_hasm);
@@ -1093,6 +1106,12 @@ int ts_problem_option(ts_problem* pr, int key, int value) {
     if (value != TS_ELEMENT64_NATIVE && value != TS_ELEMENT64_DOUBLEFLOAT)
       return fail(TS_ERR_ARG, "unknown TS_OPT_ELEMENT64 value");
     pr->elem64 = value;
+    return 0;
+  }
+  if (key == TS_OPT_TAU_WARM) {
+    if (value != 0 && value != 1) return fail(TS_ERR_ARG, "TS_OPT_TAU_WARM takes 0 or 1");
+    pr->tau_warm = value;
+    pr->vcache_valid = false;
     return 0;
   }
   if (key == TS_OPT_FP32_TANGENT) {
@@ -1901,6 +1920,17 @@ int ts_solve(ts_problem* pr, void* y_inout, const ts_solve_opts* opts, ts_solve_
   if (o.precond < 0 || o.precond > 3) return fail(TS_ERR_ARG, "ts_solve: precond must be 0, 1, 2 or 3");
   std::memset(rep, 0, sizeof(*rep));
   TS_TRY(sync_dmask(pr));
+  // the solve's own residuals start tau's eigensolve from the previous step's
+  // eigenvectors (TS_OPT_TAU_WARM); the caller's setting returns on exit
+  struct WarmGuard {
+    ts_problem* p;
+    int saved;
+    ~WarmGuard() {
+      p->tau_warm = saved;
+      if (!saved) p->vcache_valid = false;
+    }
+  } warm_guard{pr, pr->tau_warm};
+  pr->tau_warm = 1;
   const int64_t n = field_len(pr);
   const int m = o.krylov;
   if (pr->basis_m < m + 1) {
@@ -1940,8 +1970,13 @@ int ts_solve(ts_problem* pr, void* y_inout, const ts_solve_opts* opts, ts_solve_
     double t0 = now_s();
     TS_TRY(ts_residual(pr, y, pr->d_r, 64, st));
     double rn;
-    TS_TRY(dnorm(pr, pr->d_r, n, st, &rn));
+    TS_TRY(dnorm(pr, pr->d_r, n, st, &rn));   // synchronises: the residual's events are complete
     rep->t_residual += now_s() - t0;
+    {
+      float ms = 0.f;
+      if (pr->sev_res && cudaEventElapsedTime(&ms, pr->sev[0], pr->sev[1]) == cudaSuccess) rep->t_tau += ms * 1e-3;
+      ++rep->n_residual;
+    }
     if (!std::isfinite(rn)) {
       status = fail(TS_ERR_NAN, "ts_solve: non-finite residual norm");
       break;

@@ -322,10 +322,20 @@ __global__ void __launch_bounds__(256)
 // with z read as it stands (earlier colours of this sweep already updated).
 // Binv: inverted nodal diagonal blocks, column-major (precond.cu).  One warp
 // per row.  A colour holds only a few thousand rows (a few warps per SM), so
-// each warp keeps SGS_STAGES - 1 connections in flight: a ring of
-// SGS_STAGES shared-memory slots, each one record plus z_B, filled by
-// asynchronous copies while the oldest slot is multiplied.
+// each warp keeps SGS_STAGES - 1 copies in flight through a ring of
+// SGS_STAGES shared-memory slots: first the row's connections (one record
+// plus z_B per slot), then its inverted block in chunks of whole columns, so
+// that the block is already on its way while the last connections are
+// multiplied.  The terms of every output are added in the same order as a
+// plain loop over the connections and then over the block's columns.
 constexpr int SGS_STAGES = 4;
+
+template <int N>
+struct SgsChunks {
+  static constexpr int NB = 8 * N;
+  static constexpr int CPC = AsmLayout<N>::PWARP / NB;     // block columns per slot
+  static constexpr int NCH = (NB + CPC - 1) / CPC;         // chunks per block
+};
 
 template <int N>
 __global__ void __launch_bounds__(256)
@@ -334,17 +344,25 @@ __global__ void __launch_bounds__(256)
                       const float* __restrict__ binv, const uint8_t* __restrict__ dmask,
                       const float* __restrict__ r, float* __restrict__ z, int diag_only) {
   using L = AsmLayout<N>;
+  using K = SgsChunks<N>;
   constexpr int C = L::C, CC = L::CC, HB = L::HB, NB = 4 * C, S = SGS_STAGES;
+  constexpr int CPC = K::CPC, NCH = K::NCH;
   constexpr int R = (NB + 31) / 32;
+  static_assert(CPC >= 1 && (CPC * NB) % 4 == 0, "block chunk must be whole 16-byte copies");
   extern __shared__ __align__(16) float smem_f[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
-  float* buf0 = smem_f + warp * S * L::PWARP;   // [S][HB + NB]
+  float* buf0 = smem_f + warp * S * L::PWARP;   // [S][PWARP]
   for (int64_t k = (int64_t)blockIdx.x * wpb + warp; k < n_rows; k += (int64_t)gridDim.x * wpb) {
     const int A = rows[k];
-    float acc[R];
+    const bool dirA = dmask[A] != 0;
+    float acc[R], rv[R];
 #pragma unroll
-    for (int j = 0; j < R; ++j) acc[j] = 0.f;
+    for (int j = 0; j < R; ++j) {
+      const int o = lane + 32 * j;
+      acc[j] = 0.f;
+      rv[j] = o < NB ? r[(int64_t)A * NB + o] : 0.f;
+    }
     const int r0 = row_off[A], r1 = row_off[A + 1];
     // position of the diagonal connection in the row (rows hold at most a
     // few dozen connections): the i-th off-diagonal one is r0 + i, or
@@ -359,94 +377,108 @@ __global__ void __launch_bounds__(256)
     }
     // diag_only: every z_B is zero (the sweep's first colour), so is the sum
     const int n_off = diag_only ? 0 : (r1 - r0) - (pd < r1 ? 1 : 0);
+    const int n_items = n_off + NCH;
     auto conn = [&](int i) { return r0 + i + (r0 + i >= pd ? 1 : 0); };
+    const float* Bi = binv + (int64_t)A * NB * NB;
     // one commit group per ring position, empty past the row's end, so that
     // waiting for all but the newest S - 1 groups always means "slot i landed"
     auto stage = [&](int i) {
+      float* dst = buf0 + (i % S) * L::PWARP;
       if (i < n_off) {
         const int p = conn(i);
-        float* dst = buf0 + (i % S) * L::PWARP;
         const float4* src = reinterpret_cast<const float4*>(H + (int64_t)p * HB);
         for (int t = lane; t < HB / 4; t += 32) cp_async16(dst + 4 * t, src + t);
         const float4* zb = reinterpret_cast<const float4*>(z + (int64_t)cols[p] * NB);
         for (int t = lane; t < NB / 4; t += 32) cp_async16(dst + HB + 4 * t, zb + t);
+      } else if (i < n_items) {
+        const int c0 = (i - n_off) * CPC;
+        const int ncol = NB - c0 < CPC ? NB - c0 : CPC;
+        const float4* src = reinterpret_cast<const float4*>(Bi + (int64_t)c0 * NB);
+        for (int t = lane; t < ncol * NB / 4; t += 32) cp_async16(dst + 4 * t, src + t);
       }
       cp_async_commit();
     };
 #pragma unroll
     for (int i = 0; i < S - 1; ++i) stage(i);
-    for (int i = 0; i < n_off; ++i) {
-      // slot (i + S - 1) % S was multiplied in iteration i - 1 (synced below)
+    float tv[R], out[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) tv[j] = out[j] = 0.f;
+    for (int i = 0; i < n_items; ++i) {
+      // slot (i + S - 1) % S was used in iteration i - 1 (synced below)
       stage(i + S - 1);
       cp_async_wait<S - 1>();
       __syncwarp();
       float* rec = buf0 + (i % S) * L::PWARP;
-      float* xs = rec + HB;
-      const bool dirB = dmask[cols[conn(i)]] != 0;
-      for (int t = lane; t < NB; t += 32) {
-        const int f = t / C, c = t - f * C;
-        if (c == 1 || (dirB && f < 3)) xs[t] = 0.f;
-      }
-      __syncwarp();
+      if (i < n_off) {
+        float* xs = rec + HB;
+        const bool dirB = dmask[cols[conn(i)]] != 0;
+        for (int t = lane; t < NB; t += 32) {
+          const int f = t / C, c = t - f * C;
+          if (c == 1 || (dirB && f < 3)) xs[t] = 0.f;
+        }
+        __syncwarp();
 #pragma unroll
-      for (int j = 0; j < R; ++j) {
-        const int o = lane + 32 * j;
-        if (o < NB) {
-          const int f = o / C, rr = o - f * C;
-          float s = acc[j];
-          if (f < 3) {
-            const float2* Kr = reinterpret_cast<const float2*>(rec + rr * C);
-            const float2* xi = reinterpret_cast<const float2*>(xs + f * C);
+        for (int j = 0; j < R; ++j) {
+          const int o = lane + 32 * j;
+          if (o < NB) {
+            const int f = o / C, rr = o - f * C;
+            float s = acc[j];
+            if (f < 3) {
+              const float2* Kr = reinterpret_cast<const float2*>(rec + rr * C);
+              const float2* xi = reinterpret_cast<const float2*>(xs + f * C);
 #pragma unroll
-            for (int c = 0; c < C / 2; ++c) {
-              const float2 a = Kr[c], b = xi[c];
-              s = fmaf(a.x, b.x, fmaf(a.y, b.y, s));
+              for (int c = 0; c < C / 2; ++c) {
+                const float2 a = Kr[c], b = xi[c];
+                s = fmaf(a.x, b.x, fmaf(a.y, b.y, s));
+              }
+              s = fmaf(rec[2 * CC + f], xs[3 * C + rr], s);
+            } else {
+              const float2* Lr = reinterpret_cast<const float2*>(rec + CC + rr * C);
+              const float2* xp = reinterpret_cast<const float2*>(xs + 3 * C);
+#pragma unroll
+              for (int c = 0; c < C / 2; ++c) {
+                const float2 a = Lr[c], b = xp[c];
+                s = fmaf(a.x, b.x, fmaf(a.y, b.y, s));
+              }
+              s = fmaf(rec[2 * CC + 3], xs[rr], s);
+              s = fmaf(rec[2 * CC + 4], xs[C + rr], s);
+              s = fmaf(rec[2 * CC + 5], xs[2 * C + rr], s);
             }
-            s = fmaf(rec[2 * CC + f], xs[3 * C + rr], s);
-          } else {
-            const float2* Lr = reinterpret_cast<const float2*>(rec + CC + rr * C);
-            const float2* xp = reinterpret_cast<const float2*>(xs + 3 * C);
-#pragma unroll
-            for (int c = 0; c < C / 2; ++c) {
-              const float2 a = Lr[c], b = xp[c];
-              s = fmaf(a.x, b.x, fmaf(a.y, b.y, s));
-            }
-            s = fmaf(rec[2 * CC + 3], xs[rr], s);
-            s = fmaf(rec[2 * CC + 4], xs[C + rr], s);
-            s = fmaf(rec[2 * CC + 5], xs[2 * C + rr], s);
+            acc[j] = s;
           }
-          acc[j] = s;
+        }
+      } else {
+        // t = r_A - (off-diagonal sum), kept in registers; each block column
+        // takes its entry of t from the lane that holds it
+        if (i == n_off) {
+#pragma unroll
+          for (int j = 0; j < R; ++j) {
+            const int o = lane + 32 * j;
+            const int f = o / C, c = o - f * C;
+            tv[j] = (o >= NB || c == 1 || (dirA && f < 3)) ? 0.f : rv[j] - acc[j];
+          }
+        }
+        const int c0 = (i - n_off) * CPC;
+        const int ncol = NB - c0 < CPC ? NB - c0 : CPC;
+        for (int u = 0; u < ncol; ++u) {
+          const int col = c0 + u;
+          float xc = 0.f;
+#pragma unroll
+          for (int j = 0; j < R; ++j) {
+            const float v = __shfl_sync(0xffffffffu, tv[j], col & 31);
+            if ((col >> 5) == j) xc = v;
+          }
+#pragma unroll
+          for (int j = 0; j < R; ++j) {
+            const int o = lane + 32 * j;
+            if (o < NB) out[j] = fmaf(rec[u * NB + o], xc, out[j]);
+          }
         }
       }
       __syncwarp();
     }
     // the groups still open are empty (positions past the row's end)
     cp_async_wait<0>();
-    __syncwarp();
-    // t = r_A - (off-diagonal sum) into the first buffer's x slot, then z_A = Binv_A t
-    float* tv = buf0 + HB;
-    const bool dirA = dmask[A] != 0;
-#pragma unroll
-    for (int j = 0; j < R; ++j) {
-      const int o = lane + 32 * j;
-      if (o < NB) {
-        const int f = o / C, c = o - f * C;
-        tv[o] = (c == 1 || (dirA && f < 3)) ? 0.f : r[(int64_t)A * NB + o] - acc[j];
-      }
-    }
-    __syncwarp();
-    const float* Bi = binv + (int64_t)A * NB * NB;
-    float out[R];
-#pragma unroll
-    for (int j = 0; j < R; ++j) out[j] = 0.f;
-    for (int col = 0; col < NB; ++col) {
-      const float xc = tv[col];
-#pragma unroll
-      for (int j = 0; j < R; ++j) {
-        const int o = lane + 32 * j;
-        if (o < NB) out[j] = fmaf(Bi[(int64_t)col * NB + o], xc, out[j]);
-      }
-    }
 #pragma unroll
     for (int j = 0; j < R; ++j) {
       const int o = lane + 32 * j;

@@ -34,11 +34,13 @@ int launch_tau_polish(const int4* tets, const double* geo, const double* y, int6
                       double* tau_out, double nu, double C_I, unsigned* n_unconverged,
                       cudaStream_t st, float* eig_out = nullptr);
 
-// the same refinement in double-float arithmetic (tau_dd.cu)
+// the same refinement in double-float arithmetic (tau_dd.cu); with vcache
+// ((2N-1)^2 floats per point) the refined eigenvectors are stored there, and
+// with warm the Jacobi sweeps start from the ones stored by the last launch
 template <int N>
 int launch_tau_dd(const int4* tets, const double* geo, const double* y, int64_t n_elem,
                   double* tau_out, double nu, double C_I, unsigned* n_unconverged,
-                  cudaStream_t st, float* eig_out = nullptr);
+                  cudaStream_t st, float* eig_out = nullptr, float* vcache = nullptr, int warm = 0);
 
 // Backflow stabilisation on one Neumann face set (tau.cu): when y_for_matrix
 // is given, first |A_n|_- at the 3 points of every face into bneg; then

@@ -100,9 +100,10 @@ struct DDLayout {
   static constexpr int GPW = 32 / N;
   static constexpr int NN = NM * NM;
   // in 8-byte words (one dd per word).  The scratch holds one C_m at a time,
-  // then the two FP32 Jacobi matrices, then the refinement's temporaries (at
-  // most two n x n matrices at once).
-  static constexpr int SCR = (2 * NN > NP * LD) ? 2 * NN : NP * LD;
+  // then the two FP32 Jacobi matrices (and, for a warm start, an FP32 n x n
+  // product), then the refinement's temporaries (at most two n x n matrices).
+  static constexpr int JAC = NP * LD + (NN + 1) / 2;
+  static constexpr int SCR = (2 * NN > JAC) ? 2 * NN : JAC;
   static constexpr int CM = 0;
   static constexpr int M = CM + SCR;        // [NM][NM] M, later B
   static constexpr int V = M + NN;          // [NM][NM] eigenvectors
@@ -122,7 +123,8 @@ __global__ void __launch_bounds__(128) tau_dd_kernel(const int4* __restrict__ te
                                                     double* __restrict__ tau_out, double nu,
                                                     double C_I,
                                                     unsigned* __restrict__ n_unconverged,
-                                                    float* __restrict__ eig_out) {
+                                                    float* __restrict__ eig_out,
+                                                    float* __restrict__ vcache, int warm) {
   using L = DDLayout<N>;
   constexpr int NP = L::NP, NM = L::NM, C = L::C, LD = L::LD, NN = L::NN, GPW = L::GPW;
   constexpr int NT = NM * (NM + 1) / 2;
@@ -253,13 +255,52 @@ __global__ void __launch_bounds__(128) tau_dd_kernel(const int4* __restrict__ te
       __syncwarp();
     }
     // FP32 Jacobi on the leading part (the scratch now holds Mf, Vf)
-    if (live)
-      for (int t = k; t < NP * NP; t += N) {
-        const int r = t / NP, s = t - r * NP;
-        Mf[r * LD + s] = (r < NM && s < NM) ? M[r * NM + s].hi : (r == s ? 1.f : 0.f);
-        Vf[r * LD + s] = (r == s) ? 1.f : 0.f;
+    if (!warm) {
+      if (live)
+        for (int t = k; t < NP * NP; t += N) {
+          const int r = t / NP, s = t - r * NP;
+          Mf[r * LD + s] = (r < NM && s < NM) ? M[r * NM + s].hi : (r == s ? 1.f : 0.f);
+          Vf[r * LD + s] = (r == s) ? 1.f : 0.f;
+        }
+      __syncwarp();
+    } else {
+      // warm start: the point's eigenvectors W of the previous evaluation
+      // (vcache) start the rotations (Vf = W) on Mf = W^T M W, which is nearly
+      // diagonal when the state moved little, so the sweeps stop early; the
+      // refinement below makes tau independent of the start up to rounding
+      float* Tf = Vf + NP * LD;   // [NM][NM]
+      const float* wc = vcache + gq * NN;
+      if (live)
+        for (int t = k; t < NP * NP; t += N) {
+          const int r = t / NP, s = t - r * NP;
+          Vf[r * LD + s] = (r < NM && s < NM) ? wc[r * NM + s] : (r == s ? 1.f : 0.f);
+        }
+      __syncwarp();
+      if (live)
+        for (int t = k; t < NN; t += N) {
+          const int r = t / NM, s = t - r * NM;
+          float acc = 0.f;
+          for (int j = 0; j < NM; ++j) acc = fmaf(M[r * NM + j].hi, Vf[j * LD + s], acc);
+          Tf[t] = acc;
+        }
+      __syncwarp();
+      if (live) {
+        for (int t = k; t < NT; t += N) {
+          int r, s;
+          tri_rs<NM>(t, r, s);
+          float acc = 0.f;
+          for (int j = 0; j < NM; ++j) acc = fmaf(Vf[j * LD + r], Tf[j * NM + s], acc);
+          Mf[r * LD + s] = acc;
+          Mf[s * LD + r] = acc;
+        }
+        for (int t = k; t < 2 * NP - 1; t += N) {   // the padding row and column
+          const int r = t < NP ? NM : t - NP, s = t < NP ? t : NM;
+          Mf[r * LD + s] = (r == s) ? 1.f : 0.f;
+          Mf[s * LD + r] = (r == s) ? 1.f : 0.f;
+        }
       }
-    __syncwarp();
+      __syncwarp();
+    }
     const bool conv32 = jacobi_group<float, N>(Mf, Vf, k, g, lane, live, red, 12, 1e-12f);
     if (live && k == 0 && !conv32) atomicAdd(n_unconverged, 1u);
     if (live)
@@ -353,6 +394,8 @@ __global__ void __launch_bounds__(128) tau_dd_kernel(const int4* __restrict__ te
     __syncwarp();
     // eigenpairs for the derivative of tau (exact tangent), when asked: the
     // refined vectors and diag(B) with the point's scale undone
+    if (live && vcache)
+      for (int t = k; t < NN; t += N) vcache[gq * NN + t] = V[t].hi;
     if (live && eig_out) {
       float* eo = eig_out + gq * Dims<N>::EIG;
       const float back = (float)(1.0 / (unscale * unscale));
@@ -440,7 +483,7 @@ __global__ void __launch_bounds__(128) tau_dd_kernel(const int4* __restrict__ te
 template <int N>
 int launch_tau_dd(const int4* tets, const double* geo, const double* y, int64_t n_elem,
                   double* tau_out, double nu, double C_I, unsigned* n_unconverged,
-                  cudaStream_t st, float* eig_out) {
+                  cudaStream_t st, float* eig_out, float* vcache, int warm) {
   using L = DDLayout<N>;
   // warps per block (1..4) that keep the most warps resident per SM: the
   // shared footprint is the limit (228 KB per SM, 1 KB of it reserved per block)
@@ -464,13 +507,14 @@ int launch_tau_dd(const int4* tets, const double* geo, const double* y, int64_t 
   if (blocks < 1) blocks = 1;
   count_launches(1);
   tau_dd_kernel<N><<<(int)blocks, warps * 32, smem, st>>>(tets, geo, y, n_qp, tau_out, nu, C_I,
-                                                          n_unconverged, eig_out);
+                                                          n_unconverged, eig_out, vcache,
+                                                          vcache != nullptr && warm);
   return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
 #define TS_INST_TAU_DD(T, N)                                                              \
   template int launch_tau_dd<N>(const int4*, const double*, const double*, int64_t, double*, \
-                                double, double, unsigned*, cudaStream_t, float*);
+                                double, double, unsigned*, cudaStream_t, float*, float*, int);
 TS_FOR_EACH_N(TS_INST_TAU_DD, double)
 
 }  // namespace ts

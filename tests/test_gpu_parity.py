@@ -206,6 +206,36 @@ def test_fp64_tau_matches_oracle_at_high_peclet(torch, scale, tau64):
     assert err <= TOL[64], err
 
 
+@pytest.mark.parametrize("name", ["pipe_N3", "pipe_N7", "junction_N4"])
+def test_warm_started_tau_matches_oracle(torch, name):
+    """TS_OPT_TAU_WARM: tau's Jacobi sweeps start from the eigenvectors of
+    the previous evaluation.  After a nearby state and after a far one
+    (velocities 30x larger, so the cached vectors are a poor start) the FP64
+    residual still meets the oracle bar, and differs from the cold
+    evaluation only by rounding; turning the option off is cold again,
+    bit for bit."""
+    case = CASES[name]()
+    y0 = _state(case, seed=21)
+    y1 = y0 + 1e-3 * _state(case, seed=22)
+    y2 = _state(case, seed=23, scale=30.0)
+    prob = op.problem_from_case(case)
+    cold = _gls(case)
+    warm = _gls(case)
+    warm.option(tau_warm=True)
+    warm.residual(to_dev(y0, torch.float64))          # cold, fills the cache
+    for y, bar in ((y1, 1e-13), (y2, TOL[64])):
+        ref = op.residual(prob, y)
+        r_cold = to_np(cold.residual(to_dev(y, torch.float64)))
+        r_warm = to_np(warm.residual(to_dev(y, torch.float64)))
+        assert rel_l2(r_warm, ref) <= TOL[64], rel_l2(r_warm, ref)
+        assert rel_l2(r_warm, r_cold) <= bar, rel_l2(r_warm, r_cold)
+    warm.option(tau_warm=False)
+    r_off = to_np(warm.residual(to_dev(y1, torch.float64)))
+    np.testing.assert_array_equal(r_off, to_np(cold.residual(to_dev(y1, torch.float64))))
+    cold.close()
+    warm.close()
+
+
 @pytest.mark.parametrize("prec", [64, 32])
 def test_backflow_stabilisation_matches_oracle(torch, prec):
     # section 2.6 term on both outlets, with a state that flows back into them
