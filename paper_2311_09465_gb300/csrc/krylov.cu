@@ -12,6 +12,7 @@ namespace ts {
 
 constexpr int RED_BLOCKS = 304;   // 2 per SM
 constexpr int RED_THREADS = 256;
+constexpr int DOT_GROUP = 4;     // basis vectors per pass over w in dots_kernel
 
 int krylov_partial_blocks() { return RED_BLOCKS; }
 
@@ -40,20 +41,22 @@ __global__ void __launch_bounds__(RED_THREADS) dots_kernel(const double* __restr
     for (int j = threadIdx.x; j < nout; j += blockDim.x) partial[(int64_t)j * gridDim.x + blockIdx.x] = 0.0;
     return;
   }
-  __shared__ double red[RED_THREADS / 32][4];
+  __shared__ double red[RED_THREADS / 32][DOT_GROUP];
   const int64_t chunk = ((n + gridDim.x - 1) / gridDim.x + 1) & ~(int64_t)1;
   const int64_t i0 = (int64_t)blockIdx.x * chunk;
   const int64_t i1 = i0 + chunk < n ? i0 + chunk : n;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double self_acc = 0;
-  for (int j0 = 0; j0 < nvec; j0 += 4) {
-    const int nj = nvec - j0 < 4 ? nvec - j0 : 4;
-    double acc[4] = {0, 0, 0, 0};
+  for (int j0 = 0; j0 < nvec; j0 += DOT_GROUP) {
+    const int nj = nvec - j0 < DOT_GROUP ? nvec - j0 : DOT_GROUP;
+    double acc[DOT_GROUP];
+#pragma unroll
+    for (int jj = 0; jj < DOT_GROUP; ++jj) acc[jj] = 0;
     if (self && j0 == 0) {
       for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         const double wi = w[i];
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj)
+        for (int jj = 0; jj < DOT_GROUP; ++jj)
           if (jj < nj) acc[jj] += basis[(int64_t)(j0 + jj) * ld + i] * wi;
         self_acc += wi * wi;
       }
@@ -61,12 +64,12 @@ __global__ void __launch_bounds__(RED_THREADS) dots_kernel(const double* __restr
       for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         const double wi = w[i];
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj)
+        for (int jj = 0; jj < DOT_GROUP; ++jj)
           if (jj < nj) acc[jj] += basis[(int64_t)(j0 + jj) * ld + i] * wi;
       }
     }
 #pragma unroll
-    for (int jj = 0; jj < 4; ++jj) {
+    for (int jj = 0; jj < DOT_GROUP; ++jj) {
       double s = warp_sum(acc[jj]);
       if (lane == 0) red[warp][jj] = s;
     }
