@@ -230,6 +230,8 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // are ignored and the same rows of y are zero.  The record and x_B of the
 // next connection are copied into shared memory (double buffer) while the
 // current one is multiplied, so a warp keeps one record in flight.
+constexpr int SPMV_WARPS = 8;   // warps (rows in flight) per block
+
 template <int N>
 __global__ void __launch_bounds__(256)
     spmv_paper_kernel(const int32_t* __restrict__ row_off, const int32_t* __restrict__ cols,
@@ -328,7 +330,8 @@ __global__ void __launch_bounds__(256)
 // that the block is already on its way while the last connections are
 // multiplied.  The terms of every output are added in the same order as a
 // plain loop over the connections and then over the block's columns.
-constexpr int SGS_STAGES = 4;
+constexpr int SGS_STAGES = 2;
+constexpr int SGS_WARPS = 2;   // warps (rows in flight) per block
 
 template <int N>
 struct SgsChunks {
@@ -494,7 +497,7 @@ int launch_sgs_colour(const int32_t* rows, int64_t n_rows, const int32_t* row_of
                       int diag_only, cudaStream_t st) {
   using L = AsmLayout<N>;
   if (n_rows <= 0) return 0;
-  int warps = 8;
+  int warps = SGS_WARPS;
   while (warps > 1 && (size_t)warps * SGS_STAGES * L::PWARP * sizeof(float) > 200 * 1024) --warps;
   const size_t smem = (size_t)warps * SGS_STAGES * L::PWARP * sizeof(float);
   if (smem > 227 * 1024) return -6;
@@ -531,7 +534,7 @@ int launch_spmv_paper(const int32_t* row_off, const int32_t* cols, const float* 
                       const float* x, float* y, int64_t n_nodes, cudaStream_t st) {
   using L = AsmLayout<N>;
   if (n_nodes <= 0) return 0;
-  const int warps = 8;
+  const int warps = SPMV_WARPS;
   const size_t smem = (size_t)warps * 2 * L::PWARP * sizeof(float);
   if (smem > 227 * 1024) return -6;
   cudaFuncSetAttribute(spmv_paper_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -69,25 +69,29 @@ __device__ __forceinline__ void tri_rs(int t, int& r, int& s) {
 // t and is not stored), three independent chains.  Within an output the
 // terms are added in the same order as a plain loop would, so the results
 // do not depend on this grouping.
-struct Dot3 {
-  dd c0, c1, c2;
+constexpr int CH = 3;   // outputs (accumulation chains) per lane pass
+
+struct DotN {
+  dd c[CH];
 };
 
-// c_x += sum_j a_x[j * as] b_x[j * bs], j = 0..cnt-1, for x = 0, 1, 2
-template <bool FF>
-__device__ __forceinline__ void dot3(Dot3& d, const dd* a0, const dd* a1, const dd* a2, int as,
-                                     const dd* b0, const dd* b1, const dd* b2, int bs, int cnt) {
+__device__ __forceinline__ void dot_zero(DotN& d) {
+#pragma unroll
+  for (int x = 0; x < CH; ++x) d.c[x] = dd{0.f, 0.f};
+}
+
+// c_x += sum_j fa(x)[j * as] fb(x)[j * bs], j = 0..cnt-1, x < CH
+template <bool FF, typename FA, typename FB>
+__device__ __forceinline__ void dotn(DotN& d, FA fa, int as, FB fb, int bs, int cnt) {
 #pragma unroll 1
   for (int j = 0; j < cnt; ++j) {
     const int ia = j * as, ib = j * bs;
-    if (FF) {
-      d.c0 = dd_fma_ff(a0[ia].hi, b0[ib].hi, d.c0);
-      d.c1 = dd_fma_ff(a1[ia].hi, b1[ib].hi, d.c1);
-      d.c2 = dd_fma_ff(a2[ia].hi, b2[ib].hi, d.c2);
-    } else {
-      d.c0 = dd_fma(a0[ia], b0[ib], d.c0);
-      d.c1 = dd_fma(a1[ia], b1[ib], d.c1);
-      d.c2 = dd_fma(a2[ia], b2[ib], d.c2);
+#pragma unroll
+    for (int x = 0; x < CH; ++x) {
+      if (FF)
+        d.c[x] = dd_fma_ff(fa(x)[ia].hi, fb(x)[ib].hi, d.c[x]);
+      else
+        d.c[x] = dd_fma(fa(x)[ia], fb(x)[ib], d.c[x]);
     }
   }
 }
@@ -228,28 +232,21 @@ __global__ void __launch_bounds__(128) tau_dd_kernel(const int4* __restrict__ te
       __syncwarp();
       if (live)
 #pragma unroll 1
-        for (int t0 = k; t0 < NT; t0 += 3 * N) {
-          int r[3], c[3];
+        for (int t0 = k; t0 < NT; t0 += CH * N) {
+          int r[CH], c[CH];
 #pragma unroll
-          for (int x = 0; x < 3; ++x) tri_rs<NM>(t0 + x * N < NT ? t0 + x * N : t0, r[x], c[x]);
-          Dot3 d;
-          if (m == 0) {
-            d.c0 = r[0] == c[0] ? diffd : dd{0.f, 0.f};
-            d.c1 = r[1] == c[1] ? diffd : dd{0.f, 0.f};
-            d.c2 = r[2] == c[2] ? diffd : dd{0.f, 0.f};
-          } else {
-            d.c0 = M[r[0] * NM + c[0]];
-            d.c1 = M[r[1] * NM + c[1]];
-            d.c2 = M[r[2] * NM + c[2]];
-          }
-          dot3<false>(d, S + r[0] * NM, S + r[1] * NM, S + r[2] * NM, 1, S + c[0] * NM, S + c[1] * NM,
-                      S + c[2] * NM, 1, NM);
-          const dd v[3] = {d.c0, d.c1, d.c2};
+          for (int x = 0; x < CH; ++x) tri_rs<NM>(t0 + x * N < NT ? t0 + x * N : t0, r[x], c[x]);
+          DotN d;
 #pragma unroll
-          for (int x = 0; x < 3; ++x)
+          for (int x = 0; x < CH; ++x)
+            d.c[x] = m == 0 ? (r[x] == c[x] ? diffd : dd{0.f, 0.f}) : M[r[x] * NM + c[x]];
+          dotn<false>(
+            d, [&](int x) { return S + r[x] * NM; }, 1, [&](int x) { return S + c[x] * NM; }, 1, NM);
+#pragma unroll
+          for (int x = 0; x < CH; ++x)
             if (t0 + x * N < NT) {
-              M[r[x] * NM + c[x]] = v[x];
-              M[c[x] * NM + r[x]] = v[x];
+              M[r[x] * NM + c[x]] = d.c[x];
+              M[c[x] * NM + r[x]] = d.c[x];
             }
         }
       __syncwarp();
@@ -313,20 +310,22 @@ __global__ void __launch_bounds__(128) tau_dd_kernel(const int4* __restrict__ te
     for (int it = 0; it < 2; ++it) {
       if (live)
 #pragma unroll 1
-        for (int t0 = k; t0 < NT; t0 += 3 * N) {
-          int r[3], c[3];
+        for (int t0 = k; t0 < NT; t0 += CH * N) {
+          int r[CH], c[CH];
 #pragma unroll
-          for (int x = 0; x < 3; ++x) tri_rs<NM>(t0 + x * N < NT ? t0 + x * N : t0, r[x], c[x]);
-          Dot3 d{dd{0.f, 0.f}, dd{0.f, 0.f}, dd{0.f, 0.f}};
+          for (int x = 0; x < CH; ++x) tri_rs<NM>(t0 + x * N < NT ? t0 + x * N : t0, r[x], c[x]);
+          DotN d;
+        dot_zero(d);
           if (it == 0)
-            dot3<true>(d, V + r[0], V + r[1], V + r[2], NM, V + c[0], V + c[1], V + c[2], NM, NM);
+            dotn<true>(
+            d, [&](int x) { return V + r[x]; }, NM, [&](int x) { return V + c[x]; }, NM, NM);
           else
-            dot3<false>(d, V + r[0], V + r[1], V + r[2], NM, V + c[0], V + c[1], V + c[2], NM, NM);
-          const dd v[3] = {d.c0, d.c1, d.c2};
+            dotn<false>(
+            d, [&](int x) { return V + r[x]; }, NM, [&](int x) { return V + c[x]; }, NM, NM);
 #pragma unroll
-          for (int x = 0; x < 3; ++x)
+          for (int x = 0; x < CH; ++x)
             if (t0 + x * N < NT) {
-              dd h = dd_scale(dd_neg(v[x]), 0.5f);
+              dd h = dd_scale(dd_neg(d.c[x]), 0.5f);
               if (r[x] == c[x]) h = dd_add_f(h, 1.5f);
               H[r[x] * NM + c[x]] = h;
               H[c[x] * NM + r[x]] = h;
@@ -335,20 +334,21 @@ __global__ void __launch_bounds__(128) tau_dd_kernel(const int4* __restrict__ te
       __syncwarp();
       if (live)
 #pragma unroll 1
-        for (int t0 = k; t0 < NN; t0 += 3 * N) {
-          int r[3], c[3];
+        for (int t0 = k; t0 < NN; t0 += CH * N) {
+          int r[CH], c[CH];
 #pragma unroll
-          for (int x = 0; x < 3; ++x) {
+          for (int x = 0; x < CH; ++x) {
             const int t = t0 + x * N < NN ? t0 + x * N : t0;
             r[x] = t / NM;
             c[x] = t - r[x] * NM;
           }
-          Dot3 d{dd{0.f, 0.f}, dd{0.f, 0.f}, dd{0.f, 0.f}};
-          dot3<false>(d, V + r[0] * NM, V + r[1] * NM, V + r[2] * NM, 1, H + c[0], H + c[1], H + c[2], NM, NM);
-          const dd v[3] = {d.c0, d.c1, d.c2};
+          DotN d;
+        dot_zero(d);
+          dotn<false>(
+            d, [&](int x) { return V + r[x] * NM; }, 1, [&](int x) { return H + c[x]; }, NM, NM);
 #pragma unroll
-          for (int x = 0; x < 3; ++x)
-            if (t0 + x * N < NN) T[t0 + x * N] = v[x];
+          for (int x = 0; x < CH; ++x)
+            if (t0 + x * N < NN) T[t0 + x * N] = d.c[x];
         }
       __syncwarp();
       if (live)
@@ -359,36 +359,38 @@ __global__ void __launch_bounds__(128) tau_dd_kernel(const int4* __restrict__ te
     dd* P = S;
     if (live)
 #pragma unroll 1
-      for (int t0 = k; t0 < NN; t0 += 3 * N) {
-        int r[3], c[3];
+      for (int t0 = k; t0 < NN; t0 += CH * N) {
+        int r[CH], c[CH];
 #pragma unroll
-        for (int x = 0; x < 3; ++x) {
+        for (int x = 0; x < CH; ++x) {
           const int t = t0 + x * N < NN ? t0 + x * N : t0;
           r[x] = t / NM;
           c[x] = t - r[x] * NM;
         }
-        Dot3 d{dd{0.f, 0.f}, dd{0.f, 0.f}, dd{0.f, 0.f}};
-        dot3<false>(d, M + r[0] * NM, M + r[1] * NM, M + r[2] * NM, 1, V + c[0], V + c[1], V + c[2], NM, NM);
-        const dd v[3] = {d.c0, d.c1, d.c2};
+        DotN d;
+        dot_zero(d);
+        dotn<false>(
+            d, [&](int x) { return M + r[x] * NM; }, 1, [&](int x) { return V + c[x]; }, NM, NM);
 #pragma unroll
-        for (int x = 0; x < 3; ++x)
-          if (t0 + x * N < NN) P[t0 + x * N] = v[x];
+        for (int x = 0; x < CH; ++x)
+          if (t0 + x * N < NN) P[t0 + x * N] = d.c[x];
       }
     __syncwarp();
     if (live)
 #pragma unroll 1
-      for (int t0 = k; t0 < NT; t0 += 3 * N) {
-        int r[3], c[3];
+      for (int t0 = k; t0 < NT; t0 += CH * N) {
+        int r[CH], c[CH];
 #pragma unroll
-        for (int x = 0; x < 3; ++x) tri_rs<NM>(t0 + x * N < NT ? t0 + x * N : t0, r[x], c[x]);
-        Dot3 d{dd{0.f, 0.f}, dd{0.f, 0.f}, dd{0.f, 0.f}};
-        dot3<false>(d, V + r[0], V + r[1], V + r[2], NM, P + c[0], P + c[1], P + c[2], NM, NM);
-        const dd v[3] = {d.c0, d.c1, d.c2};
+        for (int x = 0; x < CH; ++x) tri_rs<NM>(t0 + x * N < NT ? t0 + x * N : t0, r[x], c[x]);
+        DotN d;
+        dot_zero(d);
+        dotn<false>(
+            d, [&](int x) { return V + r[x]; }, NM, [&](int x) { return P + c[x]; }, NM, NM);
 #pragma unroll
-        for (int x = 0; x < 3; ++x)
+        for (int x = 0; x < CH; ++x)
           if (t0 + x * N < NT) {
-            M[r[x] * NM + c[x]] = v[x];
-            M[c[x] * NM + r[x]] = v[x];
+            M[r[x] * NM + c[x]] = d.c[x];
+            M[c[x] * NM + r[x]] = d.c[x];
           }
       }
     __syncwarp();
@@ -442,36 +444,37 @@ __global__ void __launch_bounds__(128) tau_dd_kernel(const int4* __restrict__ te
     // Q = Z V^T, tau = V Q (upper triangle), undo the scale
     if (live)
 #pragma unroll 1
-      for (int t0 = k; t0 < NN; t0 += 3 * N) {
-        int r[3], c[3];
+      for (int t0 = k; t0 < NN; t0 += CH * N) {
+        int r[CH], c[CH];
 #pragma unroll
-        for (int x = 0; x < 3; ++x) {
+        for (int x = 0; x < CH; ++x) {
           const int t = t0 + x * N < NN ? t0 + x * N : t0;
           r[x] = t / NM;
           c[x] = t - r[x] * NM;
         }
-        Dot3 d{dd{0.f, 0.f}, dd{0.f, 0.f}, dd{0.f, 0.f}};
-        dot3<false>(d, Z + r[0] * NM, Z + r[1] * NM, Z + r[2] * NM, 1, V + c[0] * NM, V + c[1] * NM,
-                    V + c[2] * NM, 1, NM);
-        const dd v[3] = {d.c0, d.c1, d.c2};
+        DotN d;
+        dot_zero(d);
+        dotn<false>(
+            d, [&](int x) { return Z + r[x] * NM; }, 1, [&](int x) { return V + c[x] * NM; }, 1, NM);
 #pragma unroll
-        for (int x = 0; x < 3; ++x)
-          if (t0 + x * N < NN) Q[t0 + x * N] = v[x];
+        for (int x = 0; x < CH; ++x)
+          if (t0 + x * N < NN) Q[t0 + x * N] = d.c[x];
       }
     __syncwarp();
     if (live) {
       double* out = tau_out + gq * Dims<N>::NT_PAD;
 #pragma unroll 1
-      for (int t0 = k; t0 < NT; t0 += 3 * N) {
-        int r[3], c[3];
+      for (int t0 = k; t0 < NT; t0 += CH * N) {
+        int r[CH], c[CH];
 #pragma unroll
-        for (int x = 0; x < 3; ++x) tri_rs<NM>(t0 + x * N < NT ? t0 + x * N : t0, r[x], c[x]);
-        Dot3 d{dd{0.f, 0.f}, dd{0.f, 0.f}, dd{0.f, 0.f}};
-        dot3<false>(d, V + r[0] * NM, V + r[1] * NM, V + r[2] * NM, 1, Q + c[0], Q + c[1], Q + c[2], NM, NM);
-        const dd v[3] = {d.c0, d.c1, d.c2};
+        for (int x = 0; x < CH; ++x) tri_rs<NM>(t0 + x * N < NT ? t0 + x * N : t0, r[x], c[x]);
+        DotN d;
+        dot_zero(d);
+        dotn<false>(
+            d, [&](int x) { return V + r[x] * NM; }, 1, [&](int x) { return Q + c[x]; }, NM, NM);
 #pragma unroll
-        for (int x = 0; x < 3; ++x)
-          if (t0 + x * N < NT) out[t0 + x * N] = dd_to_double(v[x]) * unscale;
+        for (int x = 0; x < CH; ++x)
+          if (t0 + x * N < NT) out[t0 + x * N] = dd_to_double(d.c[x]) * unscale;
       }
       if (k == 0)
         for (int t = Dims<N>::NT; t < Dims<N>::NT_PAD; ++t) out[t] = 0.0;
