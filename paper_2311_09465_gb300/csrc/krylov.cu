@@ -10,7 +10,14 @@
 
 namespace ts {
 
-constexpr int RED_BLOCKS = 608;   // 4 per SM (measured: 11% less Gram-Schmidt time than 2 or 6 per SM)
+// at most 4 blocks per SM (11% less Gram-Schmidt time than 2 or 6 per SM on a
+// 2.1M-unknown field); small fields take one block per 2048 entries, so that
+// launch and reduction overheads do not grow with the grid
+constexpr int RED_BLOCKS = 608;
+static int dots_blocks(int64_t n) {
+  const int64_t b = (n + 2047) / 2048;
+  return (int)(b < 1 ? 1 : (b > RED_BLOCKS ? RED_BLOCKS : b));
+}
 constexpr int RED_THREADS = 256;
 constexpr int DOT_GROUP = 4;     // basis vectors per pass over w in dots_kernel
 
@@ -108,8 +115,9 @@ int krylov_dots(const double* basis, int64_t ld, int nvec, const double* w, int6
                 double* partial, double* h_out, cudaStream_t st, int self, const double* skip) {
   const int nout = nvec + (self ? 1 : 0);
   count_launches(2);
-  dots_kernel<<<RED_BLOCKS, RED_THREADS, 0, st>>>(basis, ld, nvec, w, n, partial, self, skip);
-  sum_partials_kernel<<<(nout + 3) / 4, 128, 0, st>>>(partial, RED_BLOCKS, nout, h_out);
+  const int nblk = dots_blocks(n);
+  dots_kernel<<<nblk, RED_THREADS, 0, st>>>(basis, ld, nvec, w, n, partial, self, skip);
+  sum_partials_kernel<<<(nout + 3) / 4, 128, 0, st>>>(partial, nblk, nout, h_out);
   return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
