@@ -23,6 +23,8 @@
 // contraction (DFT tables shared per CTA).  Elements of one colour share no
 // node, so each warp adds its 4x4xC results to the nodes without atomics;
 // the host launches the colours in order (deterministic).
+#include <type_traits>
+
 #include "common.cuh"
 #include "ddfloat.cuh"
 #include "kernels.h"
@@ -380,6 +382,9 @@ __global__ void __launch_bounds__(128)
   }
 }
 
+// warps (elements in flight) per block of the double-float element operator
+constexpr int APPLY_DD_WARPS = 4;
+
 template <typename T, int N, int MODE, typename S = T>
 static int launch_mode(const int4* tets, const S* geo, const S* v, const S* u0, const S* tau,
                        S* t0cache, const uint8_t* dmask, S* out, const S* dft, Phys<T> ph,
@@ -387,7 +392,7 @@ static int launch_mode(const int4* tets, const S* geo, const S* v, const S* u0, 
   using L = ApplyLayout<N, MODE>;
   static_assert(sizeof(T) == sizeof(S) || sizeof(T) == 8, "workspace sized by T");
   if (e1 <= e0) return 0;
-  int warps = 4;
+  int warps = std::is_same<T, ddv>::value ? APPLY_DD_WARPS : 4;
   while (warps > 1 && (size_t)(L::TABLES + warps * L::WARP) * sizeof(T) > 200 * 1024) --warps;
   const size_t smem = (size_t)(L::TABLES + warps * L::WARP) * sizeof(T);
   if (smem > 227 * 1024) return -6;
