@@ -64,11 +64,12 @@ __device__ __forceinline__ void tri_rs(int t, int& r, int& s) {
 // The double-float multiply-add is a chain of about ten dependent FP32
 // operations, and the point's shared footprint leaves only a few warps per
 // SM, so one accumulation per lane leaves the FP32 pipe idle most of the
-// time.  Each lane therefore computes three outputs of a phase at once (t,
-// t + N, t + 2N of its group's outputs; a slot past the phase's end repeats
-// t and is not stored), three independent chains.  Within an output the
-// terms are added in the same order as a plain loop would, so the results
-// do not depend on this grouping.
+// time.  Each lane therefore computes CH outputs of a phase at once (t,
+// t + N, ..., t + (CH - 1) N of its group's outputs; a slot past the phase's
+// end repeats t and is not stored), CH independent chains.  Within an output
+// the terms are added in the same order as a plain loop would, so the
+// results do not depend on this grouping (2 to 6 chains gave bit-identical
+// residuals; 3 was the fastest at N = 7).
 constexpr int CH = 3;   // outputs (accumulation chains) per lane pass
 
 struct DotN {
