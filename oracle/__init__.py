@@ -26,6 +26,7 @@ Modules:
   assemble   dense tangent H from eq. (K_mat) block by block (small meshes)
   steady     independent steady SUPG/PSPG residual (eq. NSt-weak, omega = 0)
   solver     restarted GMRES, dense LU, pseudo-time Newton (sections 2.4-2.5)
+  precond    nodal block Jacobi and symmetric block Gauss-Seidel on nodal blocks
   womersley  closed-form pulsatile pipe flow with its own Bessel series
 
 Parity status of each function is stated in its module docstring.

@@ -23,6 +23,7 @@ import numpy as np
 import pytest
 
 from oracle import operator as op
+from oracle import precond as pc
 from oracle import solver as sv
 from workloads import cases, meshgen as mg
 
@@ -126,18 +127,8 @@ def test_preconditioner_applications_match_dense_block_sweeps(name, make, varian
     Hd = sv.dense_matrix(prob, lin, "paper" if variant == "paper" else "frozen", mc).reshape(V, nb, V, nb)
     Hp = sv.dense_matrix(prob, lin, "paper", mc).reshape(V, nb, V, nb)
     fixed = _fixed_mask(case)
-    Dinv = np.empty((V, nb, nb))
-    for A in range(V):
-        B = Hd[A, :, A, :].copy()
-        B[fixed[A], :] = 0.0
-        B[:, fixed[A]] = 0.0
-        B[fixed[A], fixed[A]] = 1.0
-        Dinv[A] = np.linalg.inv(B)
-    off = Hp.copy()
-    for A in range(V):
-        off[A, fixed[A], :, :] = 0.0
-        off[:, :, A, fixed[A]] = 0.0
-        off[A, :, A, :] = 0.0
+    Dinv, _ = pc.masked_blocks(Hd, fixed)
+    _, off = pc.masked_blocks(Hp, fixed)
     x = cases.random_state(case.mesh, N, seed=8).reshape(V, nb)
     x[fixed] = 0.0
 
@@ -149,22 +140,15 @@ def test_preconditioner_applications_match_dense_block_sweeps(name, make, varian
     # block Jacobi
     g.precond_setup(2)
     zj = to_np(g.precond_apply(2, xd)).reshape(V, nb)
-    ref_j = np.einsum("aij,aj->ai", Dinv, x)
+    ref_j = pc.block_jacobi(Dinv, x)
     assert rel_l2(zj, ref_j) <= 1e-4, rel_l2(zj, ref_j)
     # symmetric block Gauss-Seidel over the node colours
     g.precond_setup(3)
     zs = to_np(g.precond_apply(3, xd)).reshape(V, nb)
     n_col, colour = g.node_colours()
     assert colour.shape == (V,) and colour.min() == 0 and colour.max() == n_col - 1
-    for A in range(V):   # a colour holds no two nodes of one element
-        nbrs = np.nonzero(np.abs(Hp[A]).sum(axis=(0, 2)) > 0)[0]
-        assert all(colour[B] != colour[A] for B in nbrs if B != A)
-    z = np.zeros((V, nb))
-    for order in (range(n_col), range(n_col - 1, -1, -1)):
-        for c in order:
-            nodes = np.nonzero(colour == c)[0]
-            t = x[nodes] - np.einsum("aibj,bj->ai", off[nodes], z)
-            z[nodes] = np.einsum("aij,aj->ai", Dinv[nodes], t)
+    assert pc.check_colouring(Hp, colour)   # a colour holds no two nodes of one element
+    z = pc.symmetric_block_gauss_seidel(Dinv, off, colour, x)
     assert rel_l2(zs, z) <= 1e-4, rel_l2(zs, z)
     assert np.all(zs[fixed] == 0.0)
     # a new residual invalidates both
