@@ -26,7 +26,8 @@ PROFILES = {"parabolic": TS_PROFILE_PARABOLIC, "womersley": TS_PROFILE_WOMERSLEY
 TS_JVP_PAPER, TS_JVP_FROZEN, TS_JVP_LIN_A, TS_JVP_EXACT = 0, 1, 2, 3
 VARIANTS = {"paper": TS_JVP_PAPER, "frozen": TS_JVP_FROZEN, "lin_a": TS_JVP_LIN_A, "exact": TS_JVP_EXACT}
 TS_OPT_TAU64, TS_OPT_FP32_TANGENT, TS_OPT_ELEMENT64, TS_OPT_TAU_WARM = 1, 2, 3, 4
-ELEMENT64 = {"native": 0, "doublefloat": 1}
+TS_ELEMENT64_NATIVE, TS_ELEMENT64_DOUBLEFLOAT = 0, 1
+ELEMENT64 = {"native": TS_ELEMENT64_NATIVE, "doublefloat": TS_ELEMENT64_DOUBLEFLOAT}
 TS_TAU64_REFINE, TS_TAU64_DOUBLEFLOAT, TS_TAU64_JACOBI = 0, 1, 2
 TAU64 = {"refine": TS_TAU64_REFINE, "doublefloat": TS_TAU64_DOUBLEFLOAT, "jacobi": TS_TAU64_JACOBI}
 SUPPORTED_N = (1, 2, 3, 4, 5, 7, 10, 15)

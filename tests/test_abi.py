@@ -53,6 +53,17 @@ def test_python_binding_mirrors_the_abi():
         assert hasattr(ts, n), n
 
 
+def test_binding_constants_match_the_header():
+    """Every integer #define TS_* of the header has the same value in the binding."""
+    import re
+    import paper_2311_09465_gb300 as ts
+    text = open(os.path.join(ROOT, "include", "tsgls.h")).read()
+    found = re.findall(r"^#define\s+(TS_\w+)\s+(-?\d+)\b", text, flags=re.M)
+    assert len(found) >= 20
+    for name, val in found:
+        assert getattr(ts, name) == int(val), name
+
+
 def _c_layout(tmp_path, structs):
     """sizeof and field offsets of the header's structs, from the C compiler."""
     import shutil
