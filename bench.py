@@ -173,6 +173,17 @@ def _jvp_bytes_model(case, b=4):
             + E * 4 * nm * (nm + 1) // 2 * b)
 
 
+def _jvp_flops(case):
+    """Algorithmic flops of one tangent product in the operator's arithmetic
+    model at N = 7 (K = 19 time samples): about 6.3k multiply-adds per
+    quadrature point (the forward and inverse time-sample transforms of the
+    convective products about 4.4k of them) and about 3k per element, i.e.
+    2 x (4 x 6300 + 3000) flops per element.  None for other N."""
+    if case.N != 7:
+        return None
+    return 2 * (4 * 6300 + 3000) * case.mesh.n_tets
+
+
 def _tau_flops(case):
     """Algorithmic flops of tau at every quadrature point (eq. 3D-tau): about
     45 n_m^3 per point -- forming M ~6 n_m^3, a Jacobi eigensolve ~30-40 n_m^3,
@@ -358,6 +369,7 @@ def run_gpu(args):
     fma_peak = 2 * alu_peak
     tau_work = _tau_dd_instr(case)
     tau_flops = _tau_flops(case)
+    jvp_flops = _jvp_flops(case)
     tau_traffic = _profile_traffic(os.path.join(csrc, "tau_dd.cu"), "tau_dd_traffic.json", "dram_bytes_per_launch")
 
     # ---- end-to-end through the public API with host buffers
@@ -405,7 +417,12 @@ def run_gpu(args):
                              "algorithmic_bytes": alg, "launch_ms": t_jel * 1e3,
                              "algorithmic_bytes_with_lin_a_tau_L": alg_lin_a,
                              "frac_with_lin_a_tau_L": alg_lin_a / t_jel / 1e9 / peak,
-                             "product_ms": t_jvp * 1e3, "peak_source": peak_kind},
+                             "product_ms": t_jvp * 1e3, "peak_source": peak_kind,
+                             "alu": None if jvp_flops is None else {
+                                 "achieved": jvp_flops / t_jel / 1e12, "peak": fma_peak, "unit": "TFLOP/s",
+                                 "frac": jvp_flops / t_jel / 1e12 / fma_peak, "flops": jvp_flops,
+                                 "flop_model": "2 x (4 x 6300 + 3000) per element at N = 7",
+                                 "peak_source": "derived FP32 FMA peak, as roofline.peak"}},
         "operator_throughput": {
             "unit": "element-mode evals/s",
             "residual_fp64": E * N / t_res64_all, "residual_fp32": E * N / t_res32,

@@ -45,6 +45,14 @@ def test_tau_flop_model():
     assert bench._tau_flops(_Case(1, 3, 4)) == 4 * 3 * 45
 
 
+def test_jvp_flop_model():
+    import bench
+    # 6.3k multiply-adds per quadrature point and 3k per element at N = 7
+    assert bench._jvp_flops(_Case(7, 187_989, 38_250)) == 2 * (4 * 6300 + 3000) * 187_989
+    assert abs(bench._jvp_flops(_Case(7, 187_989, 38_250)) - 1.06e10) < 0.01e10
+    assert bench._jvp_flops(_Case(3, 10, 5)) is None
+
+
 def test_tau_dd_instruction_model():
     import bench
     # per point at N = 7 (n = 13, t = 91): 15 instructions per double-float
